@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the FLASH hot path on GB300.
+
+Step = one all-points k-NN graph (DOPH + bucket grouping + reservoir selection
++ count-based top-k for every row) over the webspam-like workload: 350,000
+rows, D = 16,609,143, ~3,700 non-zeros per row (~1.3e9 in total), K=4, L=64,
+R=64, 2^18 buckets per table, k=128.  Inputs are seeded synthetic rows shaped
+like the paper's webspam dataset (which is not available here).
+
+Prints ONE JSON line (rank 0).  `value` is device-timed queries/s with the CSR
+already resident in HBM (5.2 GB, larger than L2, so no flush is needed);
+`e2e` is the same metric through flash_knn_graph_host with pinned host buffers
+(host->device CSR copy and device->host result copy inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl flash|reference]
+
+--impl reference times the CPU oracle (a plain single-threaded C program that
+follows the paper's algorithms step by step) on a bounded sample of the same
+workload on this machine's host cores.  Under torchrun every rank runs an
+independent replica with its own data seed (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "k-NN graph queries/sec & DOPH HBM GB/s at 1 GB300; served p50/p99 (bit-exact)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["flash", "reference"], default="flash")
+    ap.add_argument("--workload", default="webspam_like")
+    ap.add_argument("--rows", type=int, default=0, help="fewer rows (smoke runs only; the line says so)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(args, rank):
+    from paper_1709_01190_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    if args.rows:
+        w = w.scaled(args.rows)
+    if rank:
+        w = w.__class__(**{**w.__dict__, "data": w.data.replace(seed=w.data.seed + 1000 * rank)})
+    return w
+
+
+def host_data(w, pinned: bool):
+    """Generate the CSR straight into (pinned) host buffers."""
+    import torch
+    from paper_1709_01190_gb300 import synth
+    spec = w.data.replace(with_val=False)  # the method is set-based: values are never read
+    rp0 = synth.row_lengths(spec)
+    nnz = int(rp0[-1])
+    rp_t = torch.empty(spec.n_rows + 1, dtype=torch.int64, pin_memory=pinned)
+    col_t = torch.empty(max(nnz, 1), dtype=torch.int32, pin_memory=pinned)
+    csr = synth.generate(spec, row_ptr_out=rp_t.numpy(), col_out=col_t.numpy())
+    return csr, rp_t, col_t
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        pw = [num(r[3]) for r in rows if num(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons,
+                "window": "sustained warm-up loop + timed region"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(w, csr, target_s: float) -> dict:
+    """Oracle (single thread) on the first n rows of the same matrix: a full k-NN graph over them."""
+    import oracle
+    p = w.params
+
+    def run(n):
+        rp = csr.row_ptr[:n + 1]
+        col = csr.col[:int(rp[-1])]
+        t0 = time.perf_counter()
+        oracle.knn_graph(rp, col, p.K, p.L, p.R, p.range_bits, p.seed, w.k)
+        return time.perf_counter() - t0
+
+    n0 = min(csr.n_rows, 2000)
+    t0 = run(n0)
+    n = min(csr.n_rows, max(n0, int(n0 * target_s / max(t0, 1e-3))))
+    t = run(n)
+    return {"value": n / t, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} rows of the same matrix ({int(csr.row_ptr[n])} nnz): full build + all-points "
+                      f"query of those rows, plain single-threaded C oracle, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args, 0)
+    csr, _, _ = host_data(w, pinned=False)
+    import oracle
+    p = w.params
+    # bounded sample per step: sized from a short calibration so the whole run takes a few minutes
+    n0 = min(csr.n_rows, 1000)
+    t0 = time.perf_counter()
+    oracle.knn_graph(csr.row_ptr[:n0 + 1], csr.col[:int(csr.row_ptr[n0])], p.K, p.L, p.R, p.range_bits, p.seed, w.k)
+    t0 = time.perf_counter() - t0
+    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    n = min(csr.n_rows, max(n0, int(n0 * per_step / max(t0, 1e-3))))
+    rp, col = csr.row_ptr[:n + 1], csr.col[:int(csr.row_ptr[n])]
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        oracle.knn_graph(rp, col, p.K, p.L, p.R, p.range_bits, p.seed, w.k)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    ms = 1000.0 * sum(times) / len(times)
+    value = n / (ms / 1000.0)
+    sample = f"first {n} rows ({int(rp[-1])} nnz) of {w.name.split(':')[0]}: full build + all-points query"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config_of(w, csr),
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, csr):
+    p = w.params
+    return {"workload": w.name, "n_rows": csr.n_rows, "nnz": csr.nnz, "dim": csr.dim, "K": p.K, "L": p.L,
+            "R": p.R, "range_bits": p.range_bits, "k": w.k, "seed": p.seed,
+            "l2": "inputs larger than L2 (CSR of %.1f GB resident in HBM), no flush" % (
+                (8 * (csr.n_rows + 1) + 4 * csr.nnz) / 1e9)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1709_01190_gb300 as fl
+    fl.build()
+    w = workload(args, rank)
+    p = w.params
+    params = fl.FlashParams(p.K, p.L, p.R, p.range_bits, p.seed)
+    csr, rp_pin, col_pin = host_data(w, pinned=True)
+    n, nnz, k = csr.n_rows, csr.nnz, w.k
+    dev = fl.DeviceCSR(rp_pin.cuda(), col_pin[:nnz].cuda() if nnz else col_pin.cuda(), csr.dim, nnz=nnz)
+    ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    cnt = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fl.flash_knn_graph(params, dev, k, ids, cnt, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert fl.flash_device_error(stream) == 0
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    t_end = time.perf_counter() + 2.0  # sustained load so the clock samples see the kernels
+    while time.perf_counter() < t_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches_per_step = fl.flash_last_launch_count()
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1000.0)
+
+    # per-phase device times (same kernels, same launches; events on the stream between phases)
+    fl.flash_enable_phase_timing(True)
+    acc = {}
+    for _ in range(args.steps):
+        step()
+        for name, v in fl.flash_phase_times().items():
+            acc[name] = acc.get(name, 0.0) + v / args.steps
+    fl.flash_enable_phase_timing(False)
+
+    # DOPH kernels timed alone: the keys epilogue (the graph's hash phase) and the hashes output (DOPH GB/s)
+    keys_out = torch.empty((p.L, n), dtype=torch.int32, device="cuda")
+    hashes_out = torch.empty((n, p.K * p.L), dtype=torch.int32, device="cuda")
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    keys_ms = timed(lambda: fl.flash_keys(params, dev, keys_out, stream), max(args.steps, 5))
+    hash_ms = timed(lambda: fl.flash_hash(params, dev, hashes_out, stream), max(args.steps, 5))
+    del keys_out, hashes_out
+    in_bytes = 8 * (n + 1) + 4 * nnz
+    keys_bytes = in_bytes + 4 * p.L * n
+    hash_bytes = in_bytes + 4 * p.K * p.L * n
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak, peak_src = (hbm, "measured") if hbm else (6800.0, "fallback")
+    hash_phase_ms = acc.get("hash", keys_ms)
+    achieved = keys_bytes / (hash_phase_ms / 1000.0) / 1e9
+    roofline = {"kernel": "doph_kernel<keys> (hash phase of the graph step)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, torch copy read+write)",
+                "algorithmic_bytes_per_launch": keys_bytes,
+                "bytes_formula": "8(N+1) + 4 nnz + 4 L N", "traffic": None}
+    prof = os.path.join(ROOT, "profiles", "doph_keys_webspam_like_traffic.json")
+    if os.path.exists(prof) and not args.rows:
+        try:
+            with open(prof) as fh:
+                roofline["traffic"] = json.load(fh).get("traffic_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+    doph = {"GB/s": hash_bytes / (hash_ms / 1000.0) / 1e9, "ms": hash_ms, "bytes": hash_bytes,
+            "frac_of_hbm_peak": hash_bytes / (hash_ms / 1000.0) / 1e9 / peak,
+            "bytes_formula": "8(N+1) + 4 nnz + 4 K L N", "keys_epilogue_GB/s": keys_bytes / (keys_ms / 1e3) / 1e9}
+
+    e2e = None
+    if not args.no_e2e:
+        out_i = torch.empty((n, k), dtype=torch.int32, pin_memory=True).numpy()
+        out_c = torch.empty((n, k), dtype=torch.int32, pin_memory=True).numpy()
+        rp_np, col_np = rp_pin.numpy(), col_pin.numpy()[:max(nnz, 0)]
+        fl.flash_knn_graph_host(params, rp_np, col_np, csr.dim, k, out_i, out_c, stream)
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            fl.flash_knn_graph_host(params, rp_np, col_np, csr.dim, k, out_i, out_c, stream)
+        e2e_s = (time.perf_counter() - t) / args.steps
+        if world > 1:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * n / e2e_s, "unit": "queries/s", "ms_per_step": e2e_s * 1000.0,
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * n * k,
+               "api": "flash_knn_graph_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, csr, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded, webspam-shaped; see config)",
+                "config": config_of(w, csr), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+                "phases_ms": acc, "doph": doph, "reduced": bool(args.rows)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

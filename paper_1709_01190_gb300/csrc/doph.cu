@@ -1,0 +1,298 @@
+// doph.cu -- K1: densified one-permutation hashing (Section 2.3, on the
+// minwise hash of Eq. 1) of CSR rows, with MapKHashesToAddress (Section 2.2,
+// Algorithm 2) fused as an optional epilogue.
+//
+// One warp hashes one row at a time; rows are handed out dynamically in
+// small groups from a global counter, so very uneven row lengths balance.
+// Per warp, shared memory holds the row's B = K*L bins and a bitmap of the
+// non-empty bins.  Two insertion paths give identical results:
+//   dense rows  (nnz > B/2): bins start at 0xFFFFFFFF, every non-zero does a
+//       read-then-atomicMin on its bin (most reads find a smaller value and
+//       skip the atomic); the bitmap is built afterwards with ballots;
+//   sparse rows (nnz <= B/2): 32 non-zeros per round; lanes with the same bin
+//       agree on the round's minimum with __match_any_sync /
+//       __reduce_min_sync and one leader per bin updates it, so neither the
+//       bins nor any atomic on them is needed.
+// Densification (rotation): lane l owns bitmap words l, l+32, ...; it finds
+// the first non-empty bin after its word (ballot summary of non-empty
+// words) and sweeps its word downwards, writing every empty bin j as
+// v[src] + (src - j) * 0x9E3779B9 = (v[src] + src*C) - j*C.
+// Emit: the B hashes (coalesced, 16-byte stores when aligned) or the L keys.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace flash {
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct DophParams {
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int64_t n_rows, nnz;
+  uint32_t dim_u32;  // dim clipped to 2^32-1 (columns are int32)
+  uint32_t B, K, L, rb, W, G;  // W = bitmap words, G = summary words
+  uint32_t rows_per_grab;
+  uint32_t smem_words_per_warp;
+  Seeds s;
+  uint32_t *out;
+  int64_t ld;  // keys: leading dimension (>= n_rows)
+  bool vec_out;
+  uint32_t *err;
+  unsigned long long *row_counter;
+};
+
+__device__ __forceinline__ void bin_and_offset(uint32_t c, const Seeds &s, uint32_t B, uint32_t &bin,
+                                               uint32_t &off) {
+  // pi(c) = (a1*c + b1 mod 2^64) >> 32, then split the permuted range into B bins
+  uint64_t x = s.a1 * static_cast<uint64_t>(c) + s.b1;
+  uint32_t pi = static_cast<uint32_t>(x >> 32);
+  uint64_t p = static_cast<uint64_t>(pi) * B;
+  bin = static_cast<uint32_t>(p >> 32);
+  off = static_cast<uint32_t>(p);
+}
+
+__device__ __forceinline__ void insert_dense(uint32_t c, const DophParams &a, uint32_t *bins, uint32_t *mask) {
+  if (c >= a.dim_u32) {
+    raise_error(a.err, FLASH_DEVERR_COL_RANGE);
+    return;
+  }
+  uint32_t bin, off;
+  bin_and_offset(c, a.s, a.B, bin, off);
+  // bins only decrease, so a stale read is never smaller than the truth
+  if (off < *reinterpret_cast<volatile uint32_t *>(&bins[bin])) {
+    atomicMin(&bins[bin], off);
+  } else if (off == 0xFFFFFFFFu) {
+    atomicOr(&mask[bin >> 5], 1u << (bin & 31));  // non-empty although its minimum is all ones
+  }
+}
+
+// first set bit index >= from in the summary bitmap (G words), circular over W bits
+__device__ __forceinline__ int next_word_circular(const uint32_t (&sw)[4], uint32_t G, uint32_t from) {
+#pragma unroll
+  for (uint32_t g = 0; g < 4; ++g) {
+    if (g < G && g >= (from >> 5)) {
+      uint32_t m = sw[g];
+      if (g == (from >> 5)) m &= (~0u << (from & 31));
+      if (m) return static_cast<int>(32 * g + __ffs(m) - 1);
+    }
+  }
+#pragma unroll
+  for (uint32_t g = 0; g < 4; ++g) {
+    if (g < G && sw[g]) return static_cast<int>(32 * g + __ffs(sw[g]) - 1);
+  }
+  return -1;
+}
+
+template <bool KEYS>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) doph_kernel(DophParams a) {
+  extern __shared__ uint32_t smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = threadIdx.x >> 5;
+  uint32_t *bins = smem + warp * a.smem_words_per_warp;
+  uint32_t *mask = bins + a.W * 32;
+  const uint32_t B = a.B, W = a.W;
+  const uint64_t T = 1ULL << a.rb;
+
+  for (;;) {
+    unsigned long long r0 = 0;
+    if (lane == 0) r0 = atomicAdd(a.row_counter, static_cast<unsigned long long>(a.rows_per_grab));
+    r0 = __shfl_sync(kFull, r0, 0);
+    if (r0 >= static_cast<unsigned long long>(a.n_rows)) break;
+    const int64_t r_end = min(static_cast<int64_t>(r0) + a.rows_per_grab, a.n_rows);
+
+    for (int64_t r = static_cast<int64_t>(r0); r < r_end; ++r) {
+      int64_t start = a.row_ptr[r], end = a.row_ptr[r + 1];
+      if (start < 0 || end < start || end > a.nnz) {
+        if (lane == 0) raise_error(a.err, FLASH_DEVERR_ROW_PTR);
+        start = end = 0;
+      }
+      const int64_t n = end - start;
+
+      if (n == 0) {  // empty row: all-ones hashes; never inserted
+        if (KEYS) {
+          for (uint32_t t = lane; t < a.L; t += 32) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
+        } else {
+          for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = kEmptyHash;
+        }
+        continue;
+      }
+
+      const bool sparse = n <= static_cast<int64_t>(B / 2);
+      if (sparse) {
+        for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
+        __syncwarp();
+        for (int64_t base = start; base < end; base += 32) {
+          const int64_t e = base + lane;
+          bool valid = e < end;
+          uint32_t c = valid ? static_cast<uint32_t>(a.col[e]) : 0u;
+          if (valid && c >= a.dim_u32) {
+            raise_error(a.err, FLASH_DEVERR_COL_RANGE);
+            valid = false;
+          }
+          uint32_t bin = 0, off = 0;
+          if (valid) bin_and_offset(c, a.s, B, bin, off);
+          const uint32_t key = valid ? bin : 0xFFFFFFFFu;
+          const uint32_t peers = __match_any_sync(kFull, key);
+          const uint32_t mn = __reduce_min_sync(peers, off);
+          if (valid && (__ffs(peers) - 1) == static_cast<int>(lane)) {
+            const uint32_t bit = 1u << (bin & 31);
+            const uint32_t m = mask[bin >> 5];
+            bins[bin] = (m & bit) ? min(bins[bin], mn) : mn;
+            atomicOr(&mask[bin >> 5], bit);
+          }
+          __syncwarp();
+        }
+      } else {
+        for (uint32_t j = lane; j < W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
+        for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
+        __syncwarp();
+        // head up to a 16-byte boundary, 16-byte body, tail
+        const int64_t a4 = min((start + 3) & ~static_cast<int64_t>(3), end);
+        const int64_t b4 = max(a4, end & ~static_cast<int64_t>(3));
+        if (start + lane < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);
+        const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
+        const int64_t nq = (b4 - a4) >> 2;
+        int64_t q = lane;
+        for (; q + 96 < nq; q += 128) {
+          int4 v0 = __ldcs(body + q), v1 = __ldcs(body + q + 32), v2 = __ldcs(body + q + 64), v3 = __ldcs(body + q + 96);
+          insert_dense(v0.x, a, bins, mask); insert_dense(v0.y, a, bins, mask);
+          insert_dense(v0.z, a, bins, mask); insert_dense(v0.w, a, bins, mask);
+          insert_dense(v1.x, a, bins, mask); insert_dense(v1.y, a, bins, mask);
+          insert_dense(v1.z, a, bins, mask); insert_dense(v1.w, a, bins, mask);
+          insert_dense(v2.x, a, bins, mask); insert_dense(v2.y, a, bins, mask);
+          insert_dense(v2.z, a, bins, mask); insert_dense(v2.w, a, bins, mask);
+          insert_dense(v3.x, a, bins, mask); insert_dense(v3.y, a, bins, mask);
+          insert_dense(v3.z, a, bins, mask); insert_dense(v3.w, a, bins, mask);
+        }
+        for (; q < nq; q += 32) {
+          int4 v = __ldcs(body + q);
+          insert_dense(v.x, a, bins, mask); insert_dense(v.y, a, bins, mask);
+          insert_dense(v.z, a, bins, mask); insert_dense(v.w, a, bins, mask);
+        }
+        if (b4 + lane < end) insert_dense(static_cast<uint32_t>(a.col[b4 + lane]), a, bins, mask);
+        __syncwarp();
+        for (uint32_t w = 0; w < W; ++w) {
+          const uint32_t j = w * 32 + lane;
+          const bool ne = j < B && bins[j] != 0xFFFFFFFFu;
+          const uint32_t m = __ballot_sync(kFull, ne);
+          __syncwarp();
+          if (lane == 0) mask[w] |= m;
+        }
+        __syncwarp();
+      }
+
+      // ---- densification by rotation
+      uint32_t sw[4] = {0, 0, 0, 0};
+      uint32_t filled = 0;
+#pragma unroll
+      for (uint32_t g = 0; g < 4; ++g) {
+        const uint32_t w = 32 * g + lane;
+        const uint32_t m = (g < a.G && w < W) ? mask[w] : 0u;
+        filled += __popc(m);
+        sw[g] = __ballot_sync(kFull, m != 0);
+      }
+      filled = __reduce_add_sync(kFull, filled);
+      if (filled == 0) {  // every column was out of range (flagged): hash as an empty row
+        if (KEYS) {
+          for (uint32_t t = lane; t < a.L; t += 32) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
+        } else {
+          for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = kEmptyHash;
+        }
+        __syncwarp();
+        continue;
+      }
+      if (filled < B) {
+        for (uint32_t w = lane; w < W; w += 32) {
+          const int w2 = next_word_circular(sw, a.G, w + 1);
+          const uint32_t nxt = 32u * static_cast<uint32_t>(w2) + (__ffs(mask[w2]) - 1);
+          const uint32_t virt = nxt > 32u * w + 31u ? nxt : nxt + B;  // wrapped: distance counts B
+          uint32_t base = bins[nxt] + virt * kRotStep;
+          const uint32_t m = mask[w];
+#pragma unroll 8
+          for (int bit = 31; bit >= 0; --bit) {
+            const uint32_t j = 32u * w + static_cast<uint32_t>(bit);
+            if (j >= B) continue;
+            if ((m >> bit) & 1u) {
+              base = bins[j] + j * kRotStep;
+            } else {
+              bins[j] = base - j * kRotStep;
+            }
+          }
+        }
+        __syncwarp();
+      }
+
+      // ---- emit
+      if (KEYS) {
+        const int sh = 64 - static_cast<int>(a.rb);
+        for (uint32_t t = lane; t < a.L; t += 32) {
+          uint64_t x = 0;
+          for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
+          const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
+          a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+        }
+      } else if (a.vec_out) {
+        uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
+        const uint4 *src = reinterpret_cast<const uint4 *>(bins);
+        for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
+      } else {
+        for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace
+
+int launch_doph(const DophLaunch &L, cudaStream_t stream) {
+  DophParams a{};
+  a.row_ptr = L.row_ptr;
+  a.col = L.col;
+  a.n_rows = L.n_rows;
+  a.nnz = L.nnz;
+  a.dim_u32 = static_cast<uint32_t>(L.dim > 0xFFFFFFFFLL ? 0xFFFFFFFFLL : L.dim);
+  a.B = L.K * L.L;
+  a.K = L.K;
+  a.L = L.L;
+  a.rb = L.range_bits;
+  a.W = (a.B + 31) / 32;
+  a.G = (a.W + 31) / 32;
+  a.smem_words_per_warp = a.W * 32 + ((a.W + 3) & ~3u);
+  a.s = L.seeds;
+  a.out = L.out;
+  a.ld = L.ld;
+  a.vec_out = !L.keys && (a.B % 4 == 0) && ((reinterpret_cast<uintptr_t>(L.out) & 15) == 0);
+  a.err = L.err;
+  a.row_counter = L.row_counter;
+  const double avg = L.n_rows > 0 ? static_cast<double>(L.nnz) / static_cast<double>(L.n_rows) : 1.0;
+  uint32_t g = static_cast<uint32_t>(2048.0 / (avg + 16.0) + 1.0);
+  a.rows_per_grab = g < 1 ? 1 : (g > 64 ? 64 : g);
+  if (L.rows_per_grab) a.rows_per_grab = L.rows_per_grab;
+
+  if (L.n_rows == 0) return 0;
+  const size_t smem = static_cast<size_t>(kWarpsPerBlock) * a.smem_words_per_warp * sizeof(uint32_t);
+  auto kern = L.keys ? doph_kernel<true> : doph_kernel<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+    return FLASH_ECUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, smem) != cudaSuccess)
+    return FLASH_ECUDA;
+  if (per_sm < 1) return FLASH_EINVAL;
+  const int64_t warps_needed = (L.n_rows + a.rows_per_grab - 1) / a.rows_per_grab;
+  int64_t blocks = static_cast<int64_t>(per_sm) * num_sms();
+  const int64_t max_useful = (warps_needed + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (blocks > max_useful) blocks = max_useful;
+  if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
+  if (cudaMemsetAsync(L.row_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
+  kern<<<static_cast<unsigned>(blocks), kWarpsPerBlock * 32, smem, stream>>>(a);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
+}
+
+}  // namespace flash

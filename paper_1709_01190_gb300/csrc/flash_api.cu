@@ -1,0 +1,518 @@
+// flash_api.cu -- the C ABI declared in include/flash.h: argument checks,
+// scratch memory, and the order of kernel launches of every entry point.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct flash_index {
+  flash_params p;
+  flash::Seeds s;
+  int64_t n;
+  int device;
+  int32_t *ids;       // [L][n]: points grouped by bucket; reservoir = first min(m, R) of a segment
+  uint32_t *starts;   // [L][2^rb + 1]
+  int64_t bytes;
+};
+
+namespace flash {
+
+int num_sms() {
+  static thread_local int dev = -1, sms = 0;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return 1;
+  if (d != dev) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || sms < 1) sms = 1;
+    dev = d;
+  }
+  return sms;
+}
+
+namespace {
+thread_local int g_launches = 0;
+}
+void count_launches(int n) { g_launches += n; }
+void reset_launch_count() { g_launches = 0; }
+
+uint32_t *device_error_word() {
+  static std::mutex mu;
+  static std::map<int, uint32_t *> words;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = words.find(d);
+  if (it != words.end()) return it->second;
+  uint32_t *p = nullptr;
+  if (cudaMalloc(&p, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+  if (cudaMemset(p, 0, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+  words[d] = p;
+  return p;
+}
+
+namespace {
+
+std::atomic<size_t> g_scratch_budget{0};
+
+// Optional per-phase timing: when enabled, an event is recorded on the
+// call's stream before each phase and at the end; flash_phase_times()
+// returns the elapsed milliseconds between consecutive events.
+struct PhaseTimer {
+  bool enabled = false;
+  int n = 0;
+  cudaEvent_t ev[8] = {};
+  const char *names[8] = {};
+  void begin() { n = 0; }
+  void mark(const char *name, cudaStream_t s) {
+    if (!enabled || n >= 8) return;
+    if (!ev[n] && cudaEventCreate(&ev[n]) != cudaSuccess) return;
+    names[n] = name;
+    cudaEventRecord(ev[n], s);
+    ++n;
+  }
+};
+thread_local PhaseTimer g_timer;
+
+uint32_t env_u32(const char *name, uint32_t dflt) {
+  const char *v = getenv(name);
+  if (!v || !*v) return dflt;
+  return static_cast<uint32_t>(strtoul(v, nullptr, 10));
+}
+
+// One stream-ordered allocation carved into 256-byte aligned parts.
+class Arena {
+ public:
+  template <class T>
+  void add(T **ptr, int64_t count) {
+    parts_.push_back({reinterpret_cast<void **>(ptr), total_});
+    total_ += (static_cast<size_t>(count > 0 ? count : 1) * sizeof(T) + 255) & ~static_cast<size_t>(255);
+  }
+  size_t bytes() const { return total_; }
+  int alloc(cudaStream_t s) {
+    const size_t cap = g_scratch_budget.load();
+    if (cap && total_ > cap) return FLASH_ENOMEM;
+    if (cudaMallocAsync(&base_, total_, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FLASH_ENOMEM;
+    }
+    for (auto &p : parts_) *p.first = static_cast<char *>(base_) + p.second;
+    stream_ = s;
+    return 0;
+  }
+  ~Arena() {
+    if (base_) cudaFreeAsync(base_, stream_);
+  }
+
+ private:
+  std::vector<std::pair<void **, size_t>> parts_;
+  size_t total_ = 0;
+  void *base_ = nullptr;
+  cudaStream_t stream_ = nullptr;
+};
+
+int check_hash_params(const flash_params *p) {
+  if (!p || p->K < 1 || p->L < 1) return FLASH_EINVAL;
+  if (static_cast<uint64_t>(p->K) * p->L > kMaxBins) return FLASH_EINVAL;
+  return 0;
+}
+
+int check_params(const flash_params *p) {
+  if (int rc = check_hash_params(p)) return rc;
+  if (p->R < 1 || p->range_bits < 1 || p->range_bits > kMaxRangeBits) return FLASH_EINVAL;
+  if (static_cast<uint64_t>(p->L) * p->R > kMaxCandidates) return FLASH_EINVAL;
+  if (p->L > kMaxTablesPacked) return FLASH_EINVAL;
+  return 0;
+}
+
+int check_csr(const flash_csr *x) {
+  if (!x || x->n_rows < 0 || x->nnz < 0 || x->dim < 1) return FLASH_EINVAL;
+  if (x->n_rows > 0 && !x->row_ptr) return FLASH_EINVAL;
+  if (x->nnz > 0 && !x->col) return FLASH_EINVAL;
+  return 0;
+}
+
+DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, bool keys, uint32_t *out, int64_t ld,
+                     unsigned long long *counter) {
+  DophLaunch d{};
+  d.row_ptr = x->row_ptr;
+  d.col = x->col;
+  d.n_rows = x->n_rows;
+  d.nnz = x->nnz;
+  d.dim = x->dim;
+  d.K = p->K;
+  d.L = p->L;
+  d.range_bits = p->range_bits;
+  d.seeds = s;
+  d.keys = keys;
+  d.out = out;
+  d.ld = ld;
+  d.err = device_error_word();
+  d.row_counter = counter;
+  return d;
+}
+
+// scratch of build: keys, sorted keys, sort ping-pong, histograms, heavy list, counters
+struct BuildScratch {
+  uint32_t *keys = nullptr, *skeys = nullptr, *tkeys = nullptr, *hist = nullptr;
+  int32_t *tids = nullptr;
+  uint64_t *heavy = nullptr;
+  unsigned long long *counters = nullptr;
+  int64_t heavy_cap = 0;
+  SortPlan plan{};
+};
+
+void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n) {
+  const int64_t ln = static_cast<int64_t>(p->L) * n;
+  b.plan = make_sort_plan(p->range_bits, n, p->L);
+  b.heavy_cap = reservoir_heavy_capacity(n, p->L, p->R, p->range_bits);
+  ar.add(&b.keys, ln);
+  ar.add(&b.skeys, ln);
+  ar.add(&b.tkeys, ln);
+  ar.add(&b.tids, ln);
+  ar.add(&b.hist, b.plan.hist_words);
+  ar.add(&b.heavy, b.heavy_cap);
+  ar.add(&b.counters, 8);
+}
+
+// K1 (keys) -> K2 -> K3 into (ids, starts)
+int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildScratch &b, int32_t *ids,
+              uint32_t *starts, cudaStream_t st) {
+  const int64_t n = x->n_rows;
+  g_timer.mark("hash", st);
+  int rc = launch_doph(doph_args(p, s, x, true, b.keys, n, b.counters), st);
+  if (rc) return rc;
+  g_timer.mark("sort", st);
+  SortLaunch sl{};
+  sl.keys_in = b.keys;
+  sl.n = n;
+  sl.L = p->L;
+  sl.range_bits = p->range_bits;
+  sl.keys_out = b.skeys;
+  sl.ids_out = ids;
+  sl.tmp_keys = b.tkeys;
+  sl.tmp_ids = b.tids;
+  sl.hist = b.hist;
+  sl.starts = starts;
+  if ((rc = sort_tables(b.plan, sl, st))) return rc;
+  g_timer.mark("reservoir", st);
+  ReservoirLaunch rl{};
+  rl.ids = ids;
+  rl.starts = starts;
+  rl.n = n;
+  rl.L = p->L;
+  rl.R = p->R;
+  rl.range_bits = p->range_bits;
+  rl.r = s.r;
+  rl.heavy_count = b.counters + 1;
+  rl.heavy = b.heavy;
+  rl.heavy_cap = b.heavy_cap;
+  return launch_reservoir(rl, st);
+}
+
+QueryLaunch query_args(const flash_params *p, const uint32_t *qkeys, int64_t q_ld, int64_t nq, const int32_t *ids,
+                       const uint32_t *starts, int64_t n, int32_t k, const int32_t *exclude, bool exclude_self,
+                       int32_t *out_ids, int32_t *out_counts, unsigned long long *counters, int64_t *overflow) {
+  QueryLaunch q{};
+  q.qkeys = qkeys;
+  q.q_ld = q_ld;
+  q.nq = nq;
+  q.ids = ids;
+  q.starts = starts;
+  q.n = n;
+  q.L = p->L;
+  q.R = p->R;
+  q.range_bits = p->range_bits;
+  q.k = k;
+  q.exclude = exclude;
+  q.exclude_self = exclude_self;
+  q.out_ids = out_ids;
+  q.out_counts = out_counts;
+  q.counters = counters;
+  q.overflow = overflow;
+  q.warp_table = env_u32("FLASH_QUERY_WARP_TABLE", 0);
+  return q;
+}
+
+inline int cuda_ok(cudaError_t e) {
+  if (e == cudaSuccess) return 0;
+  cudaGetLastError();
+  return FLASH_ECUDA;
+}
+
+}  // namespace
+}  // namespace flash
+
+using namespace flash;
+
+extern "C" {
+
+int flash_hash(const flash_params *p, const flash_csr *x, uint32_t *hashes, void *stream) {
+  reset_launch_count();
+  if (int rc = check_hash_params(p)) return rc;
+  if (int rc = check_csr(x)) return rc;
+  if (x->n_rows > 0 && !hashes) return FLASH_EINVAL;
+  if (x->n_rows == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arena ar;
+  unsigned long long *counter = nullptr;
+  ar.add(&counter, 1);
+  if (int rc = ar.alloc(st)) return rc;
+  flash_params q = *p;
+  q.range_bits = 1;
+  return launch_doph(doph_args(&q, derive_seeds(p->seed), x, false, hashes, 0, counter), st);
+}
+
+int flash_keys(const flash_params *p, const flash_csr *x, uint32_t *keys, void *stream) {
+  reset_launch_count();
+  if (int rc = check_hash_params(p)) return rc;
+  if (!p || p->range_bits < 1 || p->range_bits > kMaxRangeBits) return FLASH_EINVAL;
+  if (int rc = check_csr(x)) return rc;
+  if (x->n_rows > 0 && !keys) return FLASH_EINVAL;
+  if (x->n_rows == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Arena ar;
+  unsigned long long *counter = nullptr;
+  ar.add(&counter, 1);
+  if (int rc = ar.alloc(st)) return rc;
+  return launch_doph(doph_args(p, derive_seeds(p->seed), x, true, keys, x->n_rows, counter), st);
+}
+
+int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, void *stream) {
+  reset_launch_count();
+  if (!out) return FLASH_EINVAL;
+  *out = nullptr;
+  if (int rc = check_params(p)) return rc;
+  if (int rc = check_csr(x)) return rc;
+  if (x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = x->n_rows;
+  const int64_t T1 = (1LL << p->range_bits) + 1;
+  flash_index *ix = new (std::nothrow) flash_index();
+  if (!ix) return FLASH_ENOMEM;
+  ix->p = *p;
+  ix->s = derive_seeds(p->seed);
+  ix->n = n;
+  cudaGetDevice(&ix->device);
+  const size_t ids_b = sizeof(int32_t) * static_cast<size_t>(p->L) * static_cast<size_t>(n > 0 ? n : 1);
+  const size_t st_b = sizeof(uint32_t) * static_cast<size_t>(p->L) * static_cast<size_t>(T1);
+  if (cudaMalloc(&ix->ids, ids_b) != cudaSuccess || cudaMalloc(&ix->starts, st_b) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ix->ids);
+    cudaFree(ix->starts);
+    delete ix;
+    return FLASH_ENOMEM;
+  }
+  ix->bytes = static_cast<int64_t>(ids_b + st_b);
+  int rc = 0;
+  {
+    Arena ar;
+    BuildScratch b;
+    plan_build(ar, b, p, n);
+    rc = ar.alloc(st);
+    if (!rc) rc = run_build(p, ix->s, x, b, ix->ids, ix->starts, st);
+  }
+  if (rc) {
+    cudaStreamSynchronize(st);
+    cudaFree(ix->ids);
+    cudaFree(ix->starts);
+    delete ix;
+    return rc;
+  }
+  *out = ix;
+  return 0;
+}
+
+int flash_query(const flash_index *ix, const flash_csr *q, int32_t k, const int32_t *exclude_ids, int32_t *out_ids,
+                int32_t *out_counts, void *stream) {
+  if (!ix || k < 1 || k > 1024) return FLASH_EINVAL;
+  reset_launch_count();
+  if (int rc = check_csr(q)) return rc;
+  if (q->n_rows > 0 && (!out_ids || !out_counts)) return FLASH_EINVAL;
+  if (q->n_rows == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const flash_params *p = &ix->p;
+  const int64_t nq = q->n_rows;
+  Arena ar;
+  uint32_t *qkeys = nullptr;
+  unsigned long long *counters = nullptr;
+  int64_t *overflow = nullptr;
+  ar.add(&qkeys, static_cast<int64_t>(p->L) * nq);
+  ar.add(&counters, 8);
+  ar.add(&overflow, nq);
+  if (int rc = ar.alloc(st)) return rc;
+  if (int rc = launch_doph(doph_args(p, ix->s, q, true, qkeys, nq, counters + 3), st)) return rc;
+  return launch_query(query_args(p, qkeys, nq, nq, ix->ids, ix->starts, ix->n, k, exclude_ids, false, out_ids,
+                                 out_counts, counters, overflow),
+                      st);
+}
+
+int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_t *out_ids, int32_t *out_counts,
+                    void *stream) {
+  if (int rc = check_params(p)) return rc;
+  if (int rc = check_csr(x)) return rc;
+  if (k < 1 || k > 1024) return FLASH_EINVAL;
+  reset_launch_count();
+  if (x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
+  if (x->n_rows > 0 && (!out_ids || !out_counts)) return FLASH_EINVAL;
+  if (x->n_rows == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = x->n_rows;
+  const Seeds s = derive_seeds(p->seed);
+  Arena ar;
+  BuildScratch b;
+  plan_build(ar, b, p, n);
+  int32_t *ids = nullptr;
+  uint32_t *starts = nullptr;
+  int64_t *overflow = nullptr;
+  ar.add(&ids, static_cast<int64_t>(p->L) * n);
+  ar.add(&starts, static_cast<int64_t>(p->L) * ((1LL << p->range_bits) + 1));
+  ar.add(&overflow, n);
+  if (int rc = ar.alloc(st)) return rc;
+  g_timer.begin();
+  if (int rc = run_build(p, s, x, b, ids, starts, st)) return rc;
+  g_timer.mark("query", st);
+  const int rc = launch_query(query_args(p, b.keys, n, n, ids, starts, n, k, nullptr, true, out_ids, out_counts,
+                                         b.counters + 4, overflow),
+                              st);
+  g_timer.mark("end", st);
+  return rc;
+}
+
+int flash_knn_graph_host(const flash_params *p, const int64_t *row_ptr, const int32_t *col, int64_t n_rows,
+                         int64_t dim, int32_t k, int32_t *out_ids, int32_t *out_counts, void *stream) {
+  if (int rc = check_params(p)) return rc;
+  if (n_rows < 0 || dim < 1 || k < 1 || k > 1024 || (n_rows > 0 && (!row_ptr || !out_ids || !out_counts)))
+    return FLASH_EINVAL;
+  if (n_rows == 0) return 0;
+  const int64_t nnz = row_ptr[n_rows];
+  if (nnz < 0 || (nnz > 0 && !col)) return FLASH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = 0;
+  {
+    Arena ar;
+    int64_t *d_rp = nullptr;
+    int32_t *d_col = nullptr, *d_ids = nullptr, *d_cnt = nullptr;
+    ar.add(&d_rp, n_rows + 1);
+    ar.add(&d_col, nnz);
+    ar.add(&d_ids, n_rows * k);
+    ar.add(&d_cnt, n_rows * k);
+    if ((rc = ar.alloc(st))) return rc;
+    rc = cuda_ok(cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n_rows + 1), cudaMemcpyHostToDevice, st));
+    if (!rc && nnz > 0) rc = cuda_ok(cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+    flash_csr x{d_rp, d_col, nullptr, n_rows, nnz, dim};
+    if (!rc) rc = flash_knn_graph(p, &x, k, d_ids, d_cnt, stream);
+    if (!rc) rc = cuda_ok(cudaMemcpyAsync(out_ids, d_ids, sizeof(int32_t) * n_rows * k, cudaMemcpyDeviceToHost, st));
+    if (!rc)
+      rc = cuda_ok(cudaMemcpyAsync(out_counts, d_cnt, sizeof(int32_t) * n_rows * k, cudaMemcpyDeviceToHost, st));
+  }
+  const int rs = cuda_ok(cudaStreamSynchronize(st));
+  return rc ? rc : rs;
+}
+
+void flash_index_free(flash_index *ix) {
+  if (!ix) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ix->device);
+  cudaFree(ix->ids);
+  cudaFree(ix->starts);
+  cudaSetDevice(cur);
+  delete ix;
+}
+
+int flash_index_get_info(const flash_index *ix, flash_index_info *info) {
+  if (!ix || !info) return FLASH_EINVAL;
+  info->params = ix->p;
+  info->n_rows = ix->n;
+  info->bytes = ix->bytes;
+  return 0;
+}
+
+int flash_index_export(const flash_index *ix, int32_t *tables, uint32_t *counts, void *stream) {
+  if (!ix || !tables || !counts) return FLASH_EINVAL;
+  return launch_export(ix->ids, ix->starts, ix->n, ix->p.L, ix->p.R, ix->p.range_bits, tables, counts,
+                       static_cast<cudaStream_t>(stream));
+}
+
+uint32_t flash_device_error(void *stream) {
+  uint32_t *w = device_error_word();
+  if (!w) return 0xFFFFFFFFu;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 0xFFFFFFFFu;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return 0xFFFFFFFFu;
+  if (v) cudaMemset(w, 0, sizeof(uint32_t));
+  return v;
+}
+
+size_t flash_set_scratch_budget(size_t bytes) { return g_scratch_budget.exchange(bytes); }
+
+size_t flash_knn_graph_scratch_bytes(const flash_params *p, int64_t n_rows) {
+  if (check_params(p) || n_rows < 0) return 0;
+  Arena ar;
+  BuildScratch b;
+  plan_build(ar, b, p, n_rows);
+  int32_t *ids = nullptr;
+  uint32_t *starts = nullptr;
+  int64_t *overflow = nullptr;
+  ar.add(&ids, static_cast<int64_t>(p->L) * n_rows);
+  ar.add(&starts, static_cast<int64_t>(p->L) * ((1LL << p->range_bits) + 1));
+  ar.add(&overflow, n_rows);
+  return ar.bytes();
+}
+
+size_t flash_query_scratch_bytes(const flash_params *p, int64_t q_rows) {
+  if (check_hash_params(p) || q_rows < 0) return 0;
+  Arena ar;
+  uint32_t *qkeys = nullptr;
+  unsigned long long *counters = nullptr;
+  int64_t *overflow = nullptr;
+  ar.add(&qkeys, static_cast<int64_t>(p->L) * q_rows);
+  ar.add(&counters, 8);
+  ar.add(&overflow, q_rows);
+  return ar.bytes();
+}
+
+const char *flash_strerror(int status) {
+  switch (status) {
+    case FLASH_OK: return "ok";
+    case FLASH_EINVAL: return "invalid or unsupported argument";
+    case FLASH_ENOMEM: return "out of device memory or scratch budget";
+    case FLASH_ECUDA: return "CUDA runtime error";
+    case FLASH_ETIMEOUT: return "bounded device wait expired";
+    case FLASH_EDATA: return "invalid input data found on the device";
+    default: return "unknown status";
+  }
+}
+
+int flash_enable_phase_timing(int on) {
+  const int old = g_timer.enabled ? 1 : 0;
+  g_timer.enabled = on != 0;
+  return old;
+}
+
+int flash_phase_times(float *ms, const char **names, int max_phases) {
+  PhaseTimer &t = g_timer;
+  if (!t.enabled || t.n < 2) return 0;
+  if (cudaEventSynchronize(t.ev[t.n - 1]) != cudaSuccess) return -1;
+  int m = 0;
+  for (int i = 0; i + 1 < t.n && m < max_phases; ++i, ++m) {
+    float v = 0.f;
+    cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]);
+    if (ms) ms[m] = v;
+    if (names) names[m] = t.names[i];
+  }
+  return m;
+}
+
+int flash_last_launch_count(void) { return g_launches; }
+
+const char *flash_version(void) { return "flash-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// internal.h -- launchers shared between the translation units of libflash.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace flash {
+
+// Kernel launches issued by the current thread since the last reset
+// (reported by flash_last_launch_count()).
+void count_launches(int n);
+void reset_launch_count();
+
+// ---- K1: DOPH (+ optional key epilogue)
+struct DophLaunch {
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int64_t n_rows, nnz, dim;
+  uint32_t K, L, range_bits;
+  Seeds seeds;
+  bool keys;         // false: out = hashes [n_rows][K*L]; true: out = keys [L][ld]
+  uint32_t *out;
+  int64_t ld;
+  uint32_t *err;
+  unsigned long long *row_counter;  // 8 bytes of device scratch
+  uint32_t rows_per_grab;           // 0 = automatic
+  int64_t max_blocks;               // 0 = automatic
+};
+int launch_doph(const DophLaunch &l, cudaStream_t stream);
+
+// ---- K2: per-table stable radix sort of bucket addresses + bucket starts
+struct SortPlan {
+  int passes;
+  int shift[4], bits[4], nbins[4];
+  uint32_t tile;
+  int64_t tiles;          // tiles per table
+  int64_t hist_words;     // L * max_nbins * tiles
+};
+SortPlan make_sort_plan(uint32_t range_bits, int64_t n, uint32_t L);
+
+struct SortLaunch {
+  const uint32_t *keys_in;  // [L][n] bucket addresses in [0, 2^rb]; 2^rb = not inserted
+  int64_t n;
+  uint32_t L, range_bits;
+  uint32_t *keys_out;       // [L][n] sorted addresses
+  int32_t *ids_out;         // [L][n] point ids in (address, id) order
+  uint32_t *tmp_keys;       // [L][n]
+  int32_t *tmp_ids;         // [L][n]
+  uint32_t *hist;           // plan.hist_words
+  uint32_t *starts;         // [L][2^rb + 1]
+};
+int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream);
+
+// ---- K3: reservoir selection in buckets with more than R arrivals
+struct ReservoirLaunch {
+  int32_t *ids;              // [L][n], sorted; reservoirs rewritten in place
+  const uint32_t *starts;    // [L][2^rb + 1]
+  int64_t n;
+  uint32_t L, R, range_bits;
+  uint64_t r;                // reservoir key
+  unsigned long long *heavy_count;  // 8 bytes of scratch
+  uint64_t *heavy;           // list of (t << 32 | b), capacity heavy_cap
+  int64_t heavy_cap;
+};
+int64_t reservoir_heavy_capacity(int64_t n, uint32_t L, uint32_t R, uint32_t range_bits);
+int launch_reservoir(const ReservoirLaunch &l, cudaStream_t stream);
+
+// ---- K4: gather + count + top-k
+struct QueryLaunch {
+  const uint32_t *qkeys;     // [L][q_ld]
+  int64_t q_ld, nq;
+  const int32_t *ids;        // index: [L][n]
+  const uint32_t *starts;    // index: [L][2^rb + 1]
+  int64_t n;
+  uint32_t L, R, range_bits;
+  int32_t k;
+  const int32_t *exclude;    // [nq] or null
+  bool exclude_self;         // exclude id q from query q (all-points graph)
+  int32_t *out_ids, *out_counts;  // [nq][k]
+  unsigned long long *counters;   // 3 x 8 bytes of scratch
+  int64_t *overflow;         // [nq] scratch
+  uint32_t warp_table;       // 0 = automatic; else power of two
+};
+int launch_query(const QueryLaunch &l, cudaStream_t stream);
+
+// ---- dense export of the tables
+int launch_export(const int32_t *ids, const uint32_t *starts, int64_t n, uint32_t L, uint32_t R, uint32_t range_bits,
+                  int32_t *tables, uint32_t *counts, cudaStream_t stream);
+
+}  // namespace flash

@@ -1,0 +1,394 @@
+// query.cu -- K4: the Querying phase (Algorithm 3) with count-based
+// k-selection (Section 3.2, Section 3.3.2).
+//
+// For query q with bucket addresses key_t(q):
+//   gather : the reservoir of bucket key_t(q) in table t is the first
+//            min(m, R) ids of its segment in the sorted table;
+//   count  : each id's number of occurrences over the L reservoirs goes into
+//            a shared-memory open-addressing table; an entry packs
+//            (id + 1) << 8 | (count - 1) (id < 2^24 - 1, count <= L <= 256),
+//            inserted with atomicCAS and incremented with atomicAdd;
+//   select : the k largest sort keys (count - 1) << 24 | (2^24 - 1 - id),
+//            i.e. count descending then id ascending, found by a radix select
+//            over 8-bit digits (histogram, suffix sum, threshold), collected
+//            and bitonic-sorted.  The excluded id is never inserted.
+// This replaces the paper's segmented sort + CountReduce on the GPU
+// (Section 3.4.1) by one pass through shared memory; the result is the
+// unique top-k of the (count desc, id asc) order, identical to sorting.
+//
+// Two launch shapes share the code through a Group (warp or block):
+//   query_warp_kernel : one warp per query, a small table per warp; queries
+//                       whose candidate count does not fit are appended to an
+//                       overflow list;
+//   query_block_kernel: one block per overflow query, a table sized for L*R.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace flash {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kQWarps = 8;        // warps per block, warp kernel
+constexpr int kQBlockThreads = 256;
+
+struct QArgs {
+  const uint32_t *qkeys;
+  int64_t q_ld, nq;
+  const int32_t *ids;
+  const uint32_t *starts;
+  int64_t n;
+  uint32_t L, R, T;
+  int32_t k;
+  uint32_t kp;              // next power of two >= k
+  const int32_t *exclude;
+  bool exclude_self;
+  int32_t *out_ids, *out_counts;
+  unsigned long long *q_counter;
+  unsigned long long *over_count;
+  int64_t *overflow;
+  uint32_t table_words;     // capacity of the group's count table (power of two)
+  uint32_t region_words;    // shared words per group
+};
+
+struct WarpGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ int size() const { return 32; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ bool leader_warp() const { return true; }
+};
+
+struct BlockGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ int size() const { return blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ bool leader_warp() const { return threadIdx.x < 32; }
+};
+
+// shared layout of one group: [tab][pre L+1][sb L][hist 256][sel kp][misc 8]
+struct Region {
+  uint32_t *tab, *pre, *sb, *hist, *sel, *misc;
+};
+
+__device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
+  Region r;
+  r.tab = base;
+  r.pre = r.tab + a.table_words;
+  r.sb = r.pre + ((a.L + 1 + 3) & ~3u);
+  r.hist = r.sb + ((a.L + 3) & ~3u);
+  r.sel = r.hist + 256;
+  r.misc = r.sel + a.kp;
+  return r;
+}
+
+__device__ __forceinline__ uint32_t sort_key(uint32_t e) {
+  // e = (id + 1) << 8 | (count - 1)  ->  (count - 1) << 24 | (2^24 - 1 - id)
+  return ((e & 0xFFu) << 24) | (0xFFFFFFu - ((e >> 8) - 1u));
+}
+
+__device__ __forceinline__ uint32_t ilog2_pow2(uint32_t x) { return 31u - __clz(x); }
+
+// Phase A: bucket segments of the query, exclusive prefix of their sizes.
+// Returns total candidate count M (valid after the call for all members).
+template <class G>
+__device__ uint32_t gather_ranges(const G &g, const QArgs &a, const Region &r, int64_t q) {
+  for (uint32_t t = g.rank(); t < a.L; t += g.size()) {
+    const uint32_t key = a.qkeys[static_cast<int64_t>(t) * a.q_ld + q];
+    uint32_t s = 0, c = 0;
+    if (key < a.T) {
+      const uint32_t *st = a.starts + static_cast<int64_t>(t) * (static_cast<int64_t>(a.T) + 1);
+      s = st[key];
+      const uint32_t m = st[key + 1] - s;
+      c = m < a.R ? m : a.R;
+    }
+    r.sb[t] = s;
+    r.pre[t] = c;
+  }
+  g.sync();
+  if (g.leader_warp()) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t per = (a.L + 31) / 32;
+    const uint32_t lo = lane * per;
+    uint32_t sum = 0;
+    for (uint32_t i = 0; i < per; ++i)
+      if (lo + i < a.L) sum += r.pre[lo + i];
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += x;
+    }
+    uint32_t run = inc - sum;
+    for (uint32_t i = 0; i < per; ++i) {
+      if (lo + i < a.L) {
+        const uint32_t c = r.pre[lo + i];
+        r.pre[lo + i] = run;
+        run += c;
+      }
+    }
+    if (lane == 31) r.pre[a.L] = inc;
+  }
+  g.sync();
+  return r.pre[a.L];
+}
+
+template <class G>
+__device__ void write_empty(const G &g, const QArgs &a, int64_t q) {
+  for (int j = g.rank(); j < a.k; j += g.size()) {
+    a.out_ids[q * a.k + j] = -1;
+    a.out_counts[q * a.k + j] = 0;
+  }
+}
+
+// Phases B and C for a query whose M candidates fit a table of S words.
+template <class G>
+__device__ void count_and_select(const G &g, const QArgs &a, const Region &r, int64_t q, uint32_t M) {
+  uint32_t S = 64;
+  while (S < 2 * M) S <<= 1;
+  const uint32_t lg = ilog2_pow2(S);
+  for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
+  g.sync();
+
+  // ---- count (COUNTFREQUENCY)
+  const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
+  for (uint32_t idx = g.rank(); idx < M; idx += g.size()) {
+    uint32_t lo = 0, hi = a.L;  // largest t with pre[t] <= idx
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (r.pre[mid] <= idx) lo = mid; else hi = mid;
+    }
+    const int32_t id = a.ids[static_cast<int64_t>(lo) * a.n + r.sb[lo] + (idx - r.pre[lo])];
+    if (id == excl) continue;
+    const uint32_t tag = (static_cast<uint32_t>(id) + 1u) << 8;
+    uint32_t h = (static_cast<uint32_t>(id) * 0x9E3779B1u) >> (32 - lg);
+    for (;;) {
+      uint32_t cur = r.tab[h];
+      if (cur == 0) {
+        cur = atomicCAS(&r.tab[h], 0u, tag);
+        if (cur == 0) break;
+      }
+      if ((cur & ~0xFFu) == tag) {
+        atomicAdd(&r.tab[h], 1u);
+        break;
+      }
+      h = (h + 1) & (S - 1);
+    }
+  }
+  g.sync();
+
+  // ---- radix select of the k-th largest sort key (SORTBYVALUE, top k)
+  uint32_t *misc = r.misc;  // [0]=prefix [1]=pmask [2]=need [3]=done [4]=nsel
+  if (g.rank() == 0) {
+    misc[0] = 0;
+    misc[1] = 0;
+    misc[2] = static_cast<uint32_t>(a.k);
+    misc[3] = 0;
+    misc[4] = 0;
+  }
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
+    g.sync();
+    const uint32_t prefix = misc[0], pmask = misc[1];
+    for (uint32_t i = g.rank(); i < S; i += g.size()) {
+      const uint32_t e = r.tab[i];
+      if (e) {
+        const uint32_t key = sort_key(e);
+        if ((key & pmask) == prefix) atomicAdd(&r.hist[(key >> shift) & 0xFFu], 1u);
+      }
+    }
+    g.sync();
+    if (g.leader_warp()) {
+      const int lane = threadIdx.x & 31;
+      uint32_t s = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s += r.hist[lane * 8 + i];
+      uint32_t suf = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_down_sync(kFull, suf, o);
+        if (lane + o < 32) suf += x;
+      }
+      const uint32_t total = __shfl_sync(kFull, suf, 0);
+      const uint32_t need = misc[2];
+      if (pass == 0 && total <= need) {
+        if (lane == 0) misc[3] = 1;
+      } else {
+        const uint32_t ball = __ballot_sync(kFull, suf >= need);
+        const int ln = 31 - __clz(ball);
+        if (lane == ln) {
+          uint32_t cum = suf - s;
+          int d = lane * 8;
+          for (int i = 7; i >= 0; --i) {
+            const uint32_t c = r.hist[lane * 8 + i];
+            if (cum + c >= need) {
+              d = lane * 8 + i;
+              break;
+            }
+            cum += c;
+          }
+          misc[2] = need - cum;
+          misc[0] = prefix | (static_cast<uint32_t>(d) << shift);
+          misc[1] = pmask | (0xFFu << shift);
+        }
+      }
+    }
+    g.sync();
+    if (misc[3]) break;
+  }
+  const uint32_t thr = misc[3] ? 1u : misc[0];
+
+  // ---- collect and sort the winners
+  for (uint32_t i = g.rank(); i < S; i += g.size()) {
+    const uint32_t e = r.tab[i];
+    if (e) {
+      const uint32_t key = sort_key(e);
+      if (key >= thr) {
+        const uint32_t pos = atomicAdd(&misc[4], 1u);
+        if (pos < a.kp) r.sel[pos] = key;  // exactly min(k, distinct) keys reach here
+      }
+    }
+  }
+  g.sync();
+  const uint32_t nsel = misc[4] < a.kp ? misc[4] : a.kp;
+  for (uint32_t i = nsel + g.rank(); i < a.kp; i += g.size()) r.sel[i] = 0;
+  g.sync();
+  for (uint32_t size = 2; size <= a.kp; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = g.rank(); i < a.kp / 2; i += g.size()) {
+        const uint32_t lo = (i / stride) * stride * 2 + (i % stride), hi = lo + stride;
+        const bool desc = (lo & size) == 0;
+        const uint32_t x = r.sel[lo], y = r.sel[hi];
+        if ((x < y) == desc) {
+          r.sel[lo] = y;
+          r.sel[hi] = x;
+        }
+      }
+      g.sync();
+    }
+  }
+  for (int j = g.rank(); j < a.k; j += g.size()) {
+    const uint32_t key = r.sel[j];
+    a.out_ids[q * a.k + j] = key ? static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)) : -1;
+    a.out_counts[q * a.k + j] = key ? static_cast<int32_t>((key >> 24) + 1u) : 0;
+  }
+  g.sync();
+}
+
+__global__ void __launch_bounds__(kQWarps * 32) query_warp_kernel(QArgs a) {
+  extern __shared__ uint32_t smem[];
+  const WarpGroup g;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Region r = carve(smem + static_cast<size_t>(warp) * a.region_words, a);
+  for (;;) {
+    unsigned long long q = 0;
+    if (lane == 0) q = atomicAdd(a.q_counter, 1ULL);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= static_cast<unsigned long long>(a.nq)) break;
+    const uint32_t M = gather_ranges(g, a, r, static_cast<int64_t>(q));
+    if (M == 0) {
+      write_empty(g, a, static_cast<int64_t>(q));
+    } else if (2 * M > a.table_words) {
+      if (lane == 0) a.overflow[atomicAdd(a.over_count, 1ULL)] = static_cast<int64_t>(q);
+    } else {
+      count_and_select(g, a, r, static_cast<int64_t>(q), M);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kQBlockThreads) query_block_kernel(QArgs a, int all_queries) {
+  extern __shared__ uint32_t smem[];
+  const BlockGroup g;
+  const Region r = carve(smem, a);
+  const int64_t count = all_queries ? a.nq : static_cast<int64_t>(*a.over_count);
+  for (int64_t h = blockIdx.x; h < count; h += gridDim.x) {
+    const int64_t q = all_queries ? h : a.overflow[h];
+    const uint32_t M = gather_ranges(g, a, r, q);
+    if (M == 0) {
+      write_empty(g, a, q);
+      g.sync();
+    } else {
+      count_and_select(g, a, r, q, M);
+    }
+  }
+}
+
+uint32_t next_pow2(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+uint32_t region_words(const QArgs &a) {
+  return a.table_words + ((a.L + 1 + 3) & ~3u) + ((a.L + 3) & ~3u) + 256 + a.kp + 8;
+}
+
+}  // namespace
+
+int launch_query(const QueryLaunch &l, cudaStream_t stream) {
+  if (l.nq == 0) return 0;
+  QArgs a{};
+  a.qkeys = l.qkeys;
+  a.q_ld = l.q_ld;
+  a.nq = l.nq;
+  a.ids = l.ids;
+  a.starts = l.starts;
+  a.n = l.n;
+  a.L = l.L;
+  a.R = l.R;
+  a.T = 1u << l.range_bits;
+  a.k = l.k;
+  a.kp = next_pow2(static_cast<uint32_t>(l.k) < 2 ? 2 : static_cast<uint32_t>(l.k));
+  a.exclude = l.exclude;
+  a.exclude_self = l.exclude_self;
+  a.out_ids = l.out_ids;
+  a.out_counts = l.out_counts;
+  a.q_counter = l.counters;
+  a.over_count = l.counters + 1;
+  a.overflow = l.overflow;
+  if (cudaMemsetAsync(l.counters, 0, 2 * sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
+
+  const uint32_t full_table = next_pow2(2 * l.L * l.R) < 64 ? 64 : next_pow2(2 * l.L * l.R);
+  const bool warp_ok = l.k <= 256;
+  int all = 1;
+  if (warp_ok) {
+    uint32_t tw = l.warp_table ? l.warp_table : 1024u;
+    if (tw > full_table) tw = full_table;
+    a.table_words = tw;
+    a.region_words = region_words(a);
+    const size_t smem = static_cast<size_t>(kQWarps) * a.region_words * sizeof(uint32_t);
+    if (cudaFuncSetAttribute(query_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return FLASH_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, query_warp_kernel, kQWarps * 32, smem) != cudaSuccess)
+      return FLASH_ECUDA;
+    if (per_sm < 1) return FLASH_EINVAL;
+    int64_t blocks = static_cast<int64_t>(per_sm) * num_sms();
+    const int64_t useful = (l.nq + kQWarps - 1) / kQWarps;
+    if (blocks > useful) blocks = useful;
+    query_warp_kernel<<<static_cast<unsigned>(blocks), kQWarps * 32, smem, stream>>>(a);
+    count_launches(1);
+    all = 0;
+  }
+  a.table_words = full_table;
+  a.region_words = region_words(a);
+  const size_t smem_b = static_cast<size_t>(a.region_words) * sizeof(uint32_t);
+  if (cudaFuncSetAttribute(query_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem_b)) != cudaSuccess)
+    return FLASH_ECUDA;
+  int per_sm_b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, query_block_kernel, kQBlockThreads, smem_b) !=
+      cudaSuccess)
+    return FLASH_ECUDA;
+  if (per_sm_b < 1) return FLASH_EINVAL;
+  const int64_t blocks_b = static_cast<int64_t>(per_sm_b) * num_sms();
+  query_block_kernel<<<static_cast<unsigned>(blocks_b), kQBlockThreads, smem_b, stream>>>(a, all);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
+}
+
+}  // namespace flash

@@ -1,0 +1,268 @@
+"""CUDA path vs the CPU oracle, element by element (integer work: bit-exact).
+
+Every call goes through the C ABI (libflash.so) via the thin binding.  Sizes
+span several tiles / warps / row groups with ragged tails; edge cases cover
+empty rows, single non-zeros, repeated and unsorted columns, the sparse/dense
+insertion switch, bin counts that are not multiples of 4 or 32, the largest
+bin count, heavy buckets (m >> R), k beyond the candidates and the block-level
+query path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_01190_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1709_01190_gb300 as fl  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fl.build()
+    assert fl.flash_device_error() == 0
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def csr_of(rows, dim):
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.asarray(r, dtype=np.int32) for r in rows]) if rp[-1] else np.zeros(0, np.int32)
+    return synth.CSR(rp, col, None, dim)
+
+
+def params_of(w):
+    p = w.params
+    return fl.FlashParams(p.K, p.L, p.R, p.range_bits, p.seed)
+
+
+def adversarial_rows(rng, B, dim, n=300):
+    rows = [[], [0], [dim - 1], [5, 5, 5], [dim - 1, 0, 7, 7, 3]]
+    for m in (B // 2 - 1, B // 2, B // 2 + 1, B, 2 * B, 31, 32, 33, 1, 2, 3, 4, 5):
+        if m >= 0:
+            rows.append(list(rng.integers(0, dim, max(m, 0))))
+    while len(rows) < n:
+        m = int(rng.choice([0, 1, 2, 3, 17, B // 2, B // 2 + 1, int(rng.integers(0, 3 * B + 5))]))
+        r = list(rng.integers(0, dim, m))
+        if rng.random() < 0.3 and r:
+            r = r + r[: len(r) // 3]  # repeats
+        rng.shuffle(r)
+        rows.append(r)
+    return rows
+
+
+HASH_SHAPES = [(1, 1), (3, 5), (4, 16), (2, 33), (4, 64), (3, 128), (4, 256), (8, 512)]
+
+
+@pytest.mark.parametrize("K,L", HASH_SHAPES)
+def test_doph_hashes_adversarial(K, L):
+    B = K * L
+    rng = np.random.default_rng(B)
+    dim = 1 << 24
+    c = csr_of(adversarial_rows(rng, B, dim), dim)
+    p = fl.FlashParams(K, L, 4, 10, 0xABCDEF + B)
+    got = u32(fl.hash_rows(p, fl.DeviceCSR.from_host(c)))
+    exp = oracle.doph(c.row_ptr, c.col, K, L, p.seed)
+    assert np.array_equal(got, exp)
+    assert fl.flash_device_error() == 0
+
+
+def test_doph_hashes_unaligned_output_and_tail():
+    K, L = 4, 16
+    c = synth.generate(synth.WORKLOADS["tiny_plain"].data.replace(n_rows=777, n_clusters=10))
+    p = fl.FlashParams(K, L, 4, 10, 99)
+    buf = torch.empty(c.n_rows * K * L + 1, dtype=torch.int32, device="cuda")
+    view = buf[1:]  # 4-byte aligned, not 16-byte aligned: scalar store path
+    fl.flash_hash(p, fl.DeviceCSR.from_host(c), view)
+    assert np.array_equal(u32(view).reshape(c.n_rows, K * L), oracle.doph(c.row_ptr, c.col, K, L, 99))
+
+
+@pytest.mark.parametrize("name,n", [("tiny_plain", 10_000), ("webspam_like", 1500), ("url_like_batched", 20_000),
+                                    ("kdd12_like", 30_000)])
+def test_doph_hashes_workloads(name, n):
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = params_of(w)
+    got = u32(fl.hash_rows(p, fl.DeviceCSR.from_host(c)))
+    assert np.array_equal(got, oracle.doph(c.row_ptr, c.col, p.K, p.L, p.seed))
+
+
+@pytest.mark.parametrize("name,n", [("tiny_plain", 10_000), ("webspam_like", 1200), ("url_like_batched", 15_000),
+                                    ("kdd12_like", 20_000)])
+def test_keys_workloads(name, n):
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = params_of(w)
+    got = u32(fl.row_keys(p, fl.DeviceCSR.from_host(c)))
+    exp = oracle.keys(c.row_ptr, c.col, p.K, p.L, p.range_bits, p.seed)
+    empty = np.diff(c.row_ptr) == 0
+    exp[:, empty] = 1 << p.range_bits
+    assert np.array_equal(got, exp)
+
+
+def test_keys_adversarial():
+    K, L, rb = 3, 40, 7
+    rng = np.random.default_rng(3)
+    c = csr_of(adversarial_rows(rng, K * L, 1 << 20, n=500), 1 << 20)
+    p = fl.FlashParams(K, L, 4, rb, 1234)
+    got = u32(fl.row_keys(p, fl.DeviceCSR.from_host(c)))
+    exp = oracle.keys(c.row_ptr, c.col, K, L, rb, 1234)
+    exp[:, np.diff(c.row_ptr) == 0] = 1 << rb
+    assert np.array_equal(got, exp)
+
+
+BUILD_CASES = [
+    ("tiny_plain", 10_000, None),
+    ("tiny_plain", 3_001, dict(range_bits=6, R=3)),       # many heavy buckets
+    ("tiny_plain", 2_500, dict(range_bits=3, R=1)),       # R = 1, every bucket heavy
+    ("tiny_plain", 4_000, dict(range_bits=9, R=200, L=4)),  # R above every occupancy
+    ("url_like_batched", 30_000, dict(range_bits=12)),   # Zipf heavy buckets, R = 128
+    ("kdd12_like", 40_000, dict(range_bits=13, L=32)),
+]
+
+
+def _params_override(w, over):
+    p = params_of(w)
+    if over:
+        p = fl.FlashParams(over.get("K", p.K), over.get("L", p.L), over.get("R", p.R),
+                           over.get("range_bits", p.range_bits), p.seed)
+    return p
+
+
+@pytest.mark.parametrize("name,n,over", BUILD_CASES)
+def test_build_tables(name, n, over):
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = _params_override(w, over)
+    ix = fl.flash_build(p, fl.DeviceCSR.from_host(c))
+    tables, counts = ix.export()
+    et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
+    assert np.array_equal(u32(counts).reshape(ec.shape), ec)
+    assert np.array_equal(tables.cpu().numpy(), et)
+    ix.free()
+
+
+def test_build_with_empty_rows_and_edge_columns():
+    rng = np.random.default_rng(11)
+    dim = 5000
+    c = csr_of(adversarial_rows(rng, 24, dim, n=2000), dim)
+    p = fl.FlashParams(3, 8, 5, 5, 77)
+    ix = fl.flash_build(p, fl.DeviceCSR.from_host(c))
+    tables, counts = ix.export()
+    et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
+    assert np.array_equal(u32(counts).reshape(ec.shape), ec)
+    assert np.array_equal(tables.cpu().numpy(), et)
+
+
+QUERY_CASES = [
+    ("tiny_plain", 10_000, None, 10, 0),
+    ("tiny_plain", 6_000, dict(range_bits=7, R=16), 25, 0),
+    ("url_like_batched", 20_000, dict(range_bits=12), 64, 0),
+    ("url_like_batched", 20_000, dict(range_bits=12), 64, 64),   # warp table too small: block path
+    ("kdd12_like", 30_000, dict(range_bits=14), 32, 0),
+    ("tiny_plain", 3_000, dict(range_bits=5, R=8), 1, 0),
+    ("tiny_plain", 3_000, dict(range_bits=5, R=8), 300, 0),      # k > 256: block path only
+]
+
+
+@pytest.mark.parametrize("name,n,over,k,wt", QUERY_CASES)
+def test_query_sampled_rows_with_exclusion(name, n, over, k, wt, monkeypatch):
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = _params_override(w, over)
+    if wt:
+        monkeypatch.setenv("FLASH_QUERY_WARP_TABLE", str(wt))
+    dev = fl.DeviceCSR.from_host(c)
+    ix = fl.flash_build(p, dev)
+    qids = synth.sample_rows(c.n_rows, min(400, c.n_rows), seed=5)
+    sub = c.rows(qids)
+    excl = torch.from_numpy(qids.astype(np.int32)).cuda()
+    ids, cnt = fl.query(ix, fl.DeviceCSR.from_host(sub), k, excl)
+    et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
+    ei, en = oracle.query(et, ec, p.K, p.L, p.R, p.range_bits, p.seed, sub.row_ptr, sub.col, k,
+                          exclude=qids.astype(np.int32))
+    assert np.array_equal(ids.cpu().numpy(), ei)
+    assert np.array_equal(cnt.cpu().numpy(), en)
+
+
+def test_query_fresh_rows_no_exclusion():
+    w = synth.WORKLOADS["url_like_batched"].scaled(25_000, n_queries=3_000)
+    c = synth.generate(w.data)
+    qc = synth.generate(w.query_data)
+    p = _params_override(w, dict(range_bits=13))
+    ix = fl.flash_build(p, fl.DeviceCSR.from_host(c))
+    ids, cnt = fl.query(ix, fl.DeviceCSR.from_host(qc), w.k)
+    et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
+    ei, en = oracle.query(et, ec, p.K, p.L, p.R, p.range_bits, p.seed, qc.row_ptr, qc.col, w.k)
+    assert np.array_equal(ids.cpu().numpy(), ei) and np.array_equal(cnt.cpu().numpy(), en)
+
+
+@pytest.mark.parametrize("name,n,over", [("tiny_plain", 10_000, None), ("webspam_like", 2_000, dict(range_bits=12)),
+                                         ("kdd12_like", 25_000, dict(range_bits=13)),
+                                         ("url_like_batched", 12_000, dict(range_bits=11))])
+def test_knn_graph(name, n, over):
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = _params_override(w, over)
+    ids, cnt = fl.knn_graph(p, fl.DeviceCSR.from_host(c), w.k)
+    ei, en = oracle.knn_graph(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, w.k)
+    assert np.array_equal(ids.cpu().numpy(), ei)
+    assert np.array_equal(cnt.cpu().numpy(), en)
+
+
+def test_knn_graph_host_buffers_match_device():
+    w = synth.WORKLOADS["tiny_plain"].scaled(5_000)
+    c = synth.generate(w.data)
+    p = params_of(w)
+    ids, cnt = fl.knn_graph(p, fl.DeviceCSR.from_host(c), w.k)
+    hi = np.empty((c.n_rows, w.k), np.int32)
+    hc = np.empty((c.n_rows, w.k), np.int32)
+    fl.flash_knn_graph_host(p, c.row_ptr, c.col, c.dim, w.k, hi, hc)
+    assert np.array_equal(hi, ids.cpu().numpy()) and np.array_equal(hc, cnt.cpu().numpy())
+
+
+def test_graph_is_deterministic_across_runs():
+    w = synth.WORKLOADS["kdd12_like"].scaled(20_000)
+    c = synth.generate(w.data)
+    p = params_of(w)
+    dev = fl.DeviceCSR.from_host(c)
+    a = fl.knn_graph(p, dev, w.k)
+    b = fl.knn_graph(p, dev, w.k)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+# ------------------------------------------------------------------ errors
+
+def test_invalid_parameters_are_rejected_on_the_host():
+    c = fl.DeviceCSR.from_host(csr_of([[1, 2], [3]], 10))
+    out = torch.empty((2, 4), dtype=torch.int32, device="cuda")
+    for bad in (fl.FlashParams(0, 4, 4, 8, 1), fl.FlashParams(4, 0, 4, 8, 1), fl.FlashParams(4, 4, 0, 8, 1),
+                fl.FlashParams(4, 4, 4, 0, 1), fl.FlashParams(4, 4, 4, 31, 1), fl.FlashParams(64, 128, 1, 8, 1),
+                fl.FlashParams(1, 300, 2, 8, 1)):
+        with pytest.raises(fl.FlashError) as e:
+            fl.flash_knn_graph(bad, c, 4, out, out.clone())
+        assert e.value.code == 1
+    with pytest.raises(fl.FlashError):
+        fl.flash_knn_graph(fl.FlashParams(2, 2, 4, 8, 1), c, 0, out, out.clone())
+
+
+def test_bad_columns_and_row_pointers_raise_the_device_flag():
+    p = fl.FlashParams(2, 4, 4, 6, 5)
+    rp = torch.tensor([0, 2, 4], dtype=torch.int64, device="cuda")
+    col = torch.tensor([1, 50, -3, 2], dtype=torch.int32, device="cuda")
+    x = fl.DeviceCSR(rp, col, dim=10)
+    fl.hash_rows(p, x)
+    assert fl.flash_device_error() & fl.DEVERR_COL_RANGE
+    assert fl.flash_device_error() == 0
+    rp2 = torch.tensor([0, 3, 2, 9], dtype=torch.int64, device="cuda")
+    x2 = fl.DeviceCSR(rp2, col, dim=10, nnz=4)
+    h = fl.hash_rows(p, x2)
+    assert fl.flash_device_error() & fl.DEVERR_ROW_PTR
+    assert np.all(u32(h)[1:] == 0xFFFFFFFF)  # rows 1 and 2 treated as empty
