@@ -125,6 +125,24 @@ int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, vo
 int flash_query(const flash_index *index, const flash_csr *q, int32_t k, const int32_t *exclude_ids,
                 int32_t *out_ids, int32_t *out_counts, void *stream);
 
+/* flash_query without any device allocation (this entry point has no
+ * counterpart in the paper).  For callers that must not allocate device
+ * memory -- a latency-critical serving thread, where cudaMalloc can block,
+ * synchronize the device or fail under memory pressure, or a program whose
+ * device memory belongs entirely to its own pool.  Same arguments and
+ * results as flash_query; the caller provides the index and every input and
+ * output buffer.  The query's scratch lives in one library-owned device
+ * array of 64 MiB per device (held until the process exits); a call needing
+ * more (about 4*L*q_rows + 8*q_rows bytes) returns FLASH_EINVAL before
+ * launching anything.  All calls on a device share that array and it keeps
+ * the last call's contents (the counters are cleared at the start of every
+ * call), so calls that overlap on the GPU race: serialize them.  The first
+ * call on a device looks the array's device address up; make it before any
+ * stream capture.  Invalid input entries are skipped safely but are not
+ * reported through flash_device_error(). */
+int flash_query_noalloc(const flash_index *index, const flash_csr *q, int32_t k, const int32_t *exclude_ids,
+                        int32_t *out_ids, int32_t *out_counts, void *stream);
+
 /* All-points k-NN graph (Section 1 and Section 4.3): build on all rows of x,
  * then query every row against that index excluding itself, reusing the
  * addresses computed for the build.

@@ -6,6 +6,17 @@
 
 #include "common.cuh"
 
+// The index behind the opaque flash_index handle.
+struct flash_index {
+  flash_params p;
+  flash::Seeds s;
+  int64_t n;
+  int device;
+  int32_t *ids;       // [L][n]: points grouped by bucket; reservoir = first min(m, R) of a segment
+  uint32_t *starts;   // [L][2^rb + 1]
+  int64_t bytes;
+};
+
 namespace flash {
 
 // Kernel launches issued by the current thread since the last reset
