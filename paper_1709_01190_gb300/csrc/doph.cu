@@ -39,7 +39,8 @@ struct DophParams {
   uint32_t rows_per_grab;
   uint32_t smem_words_per_warp;
   Seeds s;
-  uint32_t *out;
+  uint32_t *out;      // hashes [n][B], or keys [L][ld] (may be null in keys mode)
+  uint32_t *out_rm;   // keys mode: optional row-major copy [n][L]
   int64_t ld;  // keys: leading dimension (>= n_rows)
   bool vec_out;
   uint32_t *err;
@@ -56,6 +57,16 @@ __device__ __forceinline__ void bin_and_offset(uint32_t c, const Seeds &s, uint3
   off = static_cast<uint32_t>(p);
 }
 
+// Same value as bin_and_offset in fewer instructions: with a1 = a1_hi*2^32 + a1_lo,
+// (a1*c + b1) >> 32 = ((a1_lo*c + b1) >> 32) + a1_hi*c  (mod 2^32).
+__device__ __forceinline__ void bin_and_offset_fast(uint32_t c, uint32_t a1_lo, uint32_t a1_hi, uint64_t b1,
+                                                    uint32_t B, uint32_t &bin, uint32_t &off) {
+  const uint64_t t = static_cast<uint64_t>(a1_lo) * c + b1;
+  const uint32_t pi = static_cast<uint32_t>(t >> 32) + a1_hi * c;
+  bin = __umulhi(pi, B);
+  off = pi * B;
+}
+
 __device__ __forceinline__ void insert_dense(uint32_t c, const DophParams &a, uint32_t *bins, uint32_t *mask) {
   if (c >= a.dim_u32) {
     raise_error(a.err, FLASH_DEVERR_COL_RANGE);
@@ -64,10 +75,52 @@ __device__ __forceinline__ void insert_dense(uint32_t c, const DophParams &a, ui
   uint32_t bin, off;
   bin_and_offset(c, a.s, a.B, bin, off);
   // bins only decrease, so a stale read is never smaller than the truth
-  if (off < *reinterpret_cast<volatile uint32_t *>(&bins[bin])) {
+  if (off <= *reinterpret_cast<volatile uint32_t *>(&bins[bin])) {
     atomicMin(&bins[bin], off);
-  } else if (off == 0xFFFFFFFFu) {
-    atomicOr(&mask[bin >> 5], 1u << (bin & 31));  // non-empty although its minimum is all ones
+    if (off == 0xFFFFFFFFu) atomicOr(&mask[bin >> 5], 1u << (bin & 31));  // non-empty, minimum all ones
+  }
+}
+
+// Eight non-zeros at once: hash all, read all eight bins, then update.  A
+// read may be stale (another lane or an earlier element of the batch lowered
+// the bin since): it can only be too large, which costs a redundant
+// atomicMin and never loses an update.  off == 0xFFFFFFFF can only enter an
+// untouched bin (value 0xFFFFFFFF), where it must mark the bin non-empty.
+__device__ __forceinline__ void insert8(const int4 &x, const int4 &y, const DophParams &a, uint32_t a1_lo,
+                                        uint32_t a1_hi, uint32_t *bins, uint32_t *mask) {
+  const uint32_t c[8] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
+                         static_cast<uint32_t>(x.w), static_cast<uint32_t>(y.x), static_cast<uint32_t>(y.y),
+                         static_cast<uint32_t>(y.z), static_cast<uint32_t>(y.w)};
+  const uint32_t mx = max(max(max(c[0], c[1]), max(c[2], c[3])), max(max(c[4], c[5]), max(c[6], c[7])));
+  if (mx >= a.dim_u32) {  // rare: some column out of range -- element by element
+#pragma unroll
+    for (int i = 0; i < 8; ++i) insert_dense(c[i], a, bins, mask);
+    return;
+  }
+  uint32_t bin[8], off[8], cur[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) bin_and_offset_fast(c[i], a1_lo, a1_hi, a.s.b1, a.B, bin[i], off[i]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) cur[i] = bins[bin[i]];
+  if ((a.B & 1u) == 0) {
+    // B even: off = pi*B mod 2^32 is even, never 0xFFFFFFFF, so the update is a
+    // predicated shared-memory min reduction without a branch
+    const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(bins));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %0, %1;\n\t@p red.shared.min.u32 [%2], %0;\n\t}" ::"r"(off[i]),
+          "r"(cur[i]), "r"(base + 4u * bin[i])
+          : "memory");
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (off[i] <= cur[i]) {
+      atomicMin(&bins[bin[i]], off[i]);
+      if (off[i] == 0xFFFFFFFFu) atomicOr(&mask[bin[i] >> 5], 1u << (bin[i] & 31));
+    }
   }
 }
 
@@ -89,7 +142,7 @@ __device__ __forceinline__ int next_word_circular(const uint32_t (&sw)[4], uint3
 }
 
 template <bool KEYS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) doph_kernel(DophParams a) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) doph_kernel(DophParams a) {
   extern __shared__ uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
@@ -115,7 +168,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) doph_kernel(DophParams a)
 
       if (n == 0) {  // empty row: all-ones hashes; never inserted
         if (KEYS) {
-          for (uint32_t t = lane; t < a.L; t += 32) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
+          for (uint32_t t = lane; t < a.L; t += 32) {
+            if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
+            if (a.out_rm) a.out_rm[r * a.L + t] = static_cast<uint32_t>(T);
+          }
         } else {
           for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = kEmptyHash;
         }
@@ -157,22 +213,39 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) doph_kernel(DophParams a)
         if (start + lane < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);
         const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
         const int64_t nq = (b4 - a4) >> 2;
-        int64_t q = lane;
-        for (; q + 96 < nq; q += 128) {
-          int4 v0 = __ldcs(body + q), v1 = __ldcs(body + q + 32), v2 = __ldcs(body + q + 64), v3 = __ldcs(body + q + 96);
-          insert_dense(v0.x, a, bins, mask); insert_dense(v0.y, a, bins, mask);
-          insert_dense(v0.z, a, bins, mask); insert_dense(v0.w, a, bins, mask);
-          insert_dense(v1.x, a, bins, mask); insert_dense(v1.y, a, bins, mask);
-          insert_dense(v1.z, a, bins, mask); insert_dense(v1.w, a, bins, mask);
-          insert_dense(v2.x, a, bins, mask); insert_dense(v2.y, a, bins, mask);
-          insert_dense(v2.z, a, bins, mask); insert_dense(v2.w, a, bins, mask);
-          insert_dense(v3.x, a, bins, mask); insert_dense(v3.y, a, bins, mask);
-          insert_dense(v3.z, a, bins, mask); insert_dense(v3.w, a, bins, mask);
+        const uint32_t a1_lo = static_cast<uint32_t>(a.s.a1), a1_hi = static_cast<uint32_t>(a.s.a1 >> 32);
+        // groups of 128 int4 per warp (4 per lane); the next group's loads are
+        // issued before the current group is hashed
+        const int64_t ngroups = nq >> 7;
+        int4 g0, g1, g2, g3;
+        if (ngroups > 0) {
+          g0 = __ldcs(body + lane);
+          g1 = __ldcs(body + lane + 32);
+          g2 = __ldcs(body + lane + 64);
+          g3 = __ldcs(body + lane + 96);
         }
-        for (; q < nq; q += 32) {
-          int4 v = __ldcs(body + q);
-          insert_dense(v.x, a, bins, mask); insert_dense(v.y, a, bins, mask);
-          insert_dense(v.z, a, bins, mask); insert_dense(v.w, a, bins, mask);
+        for (int64_t g = 0; g < ngroups; ++g) {
+          int4 n0 = g0, n1 = g1, n2 = g2, n3 = g3;
+          if (g + 1 < ngroups) {
+            const int4 *nb = body + ((g + 1) << 7) + lane;
+            n0 = __ldcs(nb);
+            n1 = __ldcs(nb + 32);
+            n2 = __ldcs(nb + 64);
+            n3 = __ldcs(nb + 96);
+          }
+          insert8(g0, g1, a, a1_lo, a1_hi, bins, mask);
+          insert8(g2, g3, a, a1_lo, a1_hi, bins, mask);
+          g0 = n0;
+          g1 = n1;
+          g2 = n2;
+          g3 = n3;
+        }
+        for (int64_t q = (ngroups << 7) + lane; q < nq; q += 32) {
+          const int4 v = __ldcs(body + q);
+          insert_dense(static_cast<uint32_t>(v.x), a, bins, mask);
+          insert_dense(static_cast<uint32_t>(v.y), a, bins, mask);
+          insert_dense(static_cast<uint32_t>(v.z), a, bins, mask);
+          insert_dense(static_cast<uint32_t>(v.w), a, bins, mask);
         }
         if (b4 + lane < end) insert_dense(static_cast<uint32_t>(a.col[b4 + lane]), a, bins, mask);
         __syncwarp();
@@ -199,7 +272,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) doph_kernel(DophParams a)
       filled = __reduce_add_sync(kFull, filled);
       if (filled == 0) {  // every column was out of range (flagged): hash as an empty row
         if (KEYS) {
-          for (uint32_t t = lane; t < a.L; t += 32) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
+          for (uint32_t t = lane; t < a.L; t += 32) {
+            if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
+            if (a.out_rm) a.out_rm[r * a.L + t] = static_cast<uint32_t>(T);
+          }
         } else {
           for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = kEmptyHash;
         }
@@ -234,7 +310,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) doph_kernel(DophParams a)
           uint64_t x = 0;
           for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
           const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
-          a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+          if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+          if (a.out_rm) a.out_rm[r * a.L + t] = key;
         }
       } else if (a.vec_out) {
         uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
@@ -266,6 +343,7 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.smem_words_per_warp = a.W * 32 + ((a.W + 3) & ~3u);
   a.s = L.seeds;
   a.out = L.out;
+  a.out_rm = L.out_rowmajor;
   a.ld = L.ld;
   a.vec_out = !L.keys && (a.B % 4 == 0) && ((reinterpret_cast<uintptr_t>(L.out) & 15) == 0);
   a.err = L.err;

@@ -150,6 +150,7 @@ DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, 
 // scratch of build: keys, sorted keys, sort ping-pong, histograms, heavy list, counters
 struct BuildScratch {
   uint32_t *keys = nullptr, *skeys = nullptr, *tkeys = nullptr, *hist = nullptr;
+  uint32_t *keys_rm = nullptr;  // row-major copy of the addresses (all-points graph only)
   int32_t *tids = nullptr;
   uint64_t *heavy = nullptr;
   unsigned long long *counters = nullptr;
@@ -157,11 +158,12 @@ struct BuildScratch {
   SortPlan plan{};
 };
 
-void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n) {
+void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, bool rowmajor_keys = false) {
   const int64_t ln = static_cast<int64_t>(p->L) * n;
   b.plan = make_sort_plan(p->range_bits, n, p->L);
   b.heavy_cap = reservoir_heavy_capacity(n, p->L, p->R, p->range_bits);
   ar.add(&b.keys, ln);
+  if (rowmajor_keys) ar.add(&b.keys_rm, ln);
   ar.add(&b.skeys, ln);
   ar.add(&b.tkeys, ln);
   ar.add(&b.tids, ln);
@@ -175,7 +177,9 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
               uint32_t *starts, cudaStream_t st) {
   const int64_t n = x->n_rows;
   g_timer.mark("hash", st);
-  int rc = launch_doph(doph_args(p, s, x, true, b.keys, n, b.counters), st);
+  DophLaunch dl = doph_args(p, s, x, true, b.keys, n, b.counters);
+  dl.out_rowmajor = b.keys_rm;
+  int rc = launch_doph(dl, st);
   if (rc) return rc;
   g_timer.mark("sort", st);
   SortLaunch sl{};
@@ -205,11 +209,13 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
   return launch_reservoir(rl, st);
 }
 
-QueryLaunch query_args(const flash_params *p, const uint32_t *qkeys, int64_t q_ld, int64_t nq, const int32_t *ids,
+QueryLaunch query_args(const flash_params *p, const uint32_t *qkeys, bool rowmajor, int64_t q_ld, int64_t nq,
+                       const int32_t *ids,
                        const uint32_t *starts, int64_t n, int32_t k, const int32_t *exclude, bool exclude_self,
                        int32_t *out_ids, int32_t *out_counts, unsigned long long *counters, int64_t *overflow) {
   QueryLaunch q{};
   q.qkeys = qkeys;
+  q.qkeys_rowmajor = rowmajor;
   q.q_ld = q_ld;
   q.nq = nq;
   q.ids = ids;
@@ -336,8 +342,10 @@ int flash_query(const flash_index *ix, const flash_csr *q, int32_t k, const int3
   ar.add(&counters, 8);
   ar.add(&overflow, nq);
   if (int rc = ar.alloc(st)) return rc;
-  if (int rc = launch_doph(doph_args(p, ix->s, q, true, qkeys, nq, counters + 3), st)) return rc;
-  return launch_query(query_args(p, qkeys, nq, nq, ix->ids, ix->starts, ix->n, k, exclude_ids, false, out_ids,
+  DophLaunch dl = doph_args(p, ix->s, q, true, nullptr, nq, counters + 3);
+  dl.out_rowmajor = qkeys;
+  if (int rc = launch_doph(dl, st)) return rc;
+  return launch_query(query_args(p, qkeys, true, nq, nq, ix->ids, ix->starts, ix->n, k, exclude_ids, false, out_ids,
                                  out_counts, counters, overflow),
                       st);
 }
@@ -356,7 +364,7 @@ int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_
   const Seeds s = derive_seeds(p->seed);
   Arena ar;
   BuildScratch b;
-  plan_build(ar, b, p, n);
+  plan_build(ar, b, p, n, true);
   int32_t *ids = nullptr;
   uint32_t *starts = nullptr;
   int64_t *overflow = nullptr;
@@ -367,8 +375,8 @@ int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_
   g_timer.begin();
   if (int rc = run_build(p, s, x, b, ids, starts, st)) return rc;
   g_timer.mark("query", st);
-  const int rc = launch_query(query_args(p, b.keys, n, n, ids, starts, n, k, nullptr, true, out_ids, out_counts,
-                                         b.counters + 4, overflow),
+  const int rc = launch_query(query_args(p, b.keys_rm, true, n, n, ids, starts, n, k, nullptr, true, out_ids,
+                                         out_counts, b.counters + 4, overflow),
                               st);
   g_timer.mark("end", st);
   return rc;
@@ -447,7 +455,7 @@ size_t flash_knn_graph_scratch_bytes(const flash_params *p, int64_t n_rows) {
   if (check_params(p) || n_rows < 0) return 0;
   Arena ar;
   BuildScratch b;
-  plan_build(ar, b, p, n_rows);
+  plan_build(ar, b, p, n_rows, true);
   int32_t *ids = nullptr;
   uint32_t *starts = nullptr;
   int64_t *overflow = nullptr;

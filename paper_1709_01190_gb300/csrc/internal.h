@@ -31,8 +31,9 @@ struct DophLaunch {
   int64_t n_rows, nnz, dim;
   uint32_t K, L, range_bits;
   Seeds seeds;
-  bool keys;         // false: out = hashes [n_rows][K*L]; true: out = keys [L][ld]
+  bool keys;         // false: out = hashes [n_rows][K*L]; true: out = keys [L][ld] (or null)
   uint32_t *out;
+  uint32_t *out_rowmajor;  // keys mode, optional: keys [n_rows][L]
   int64_t ld;
   uint32_t *err;
   unsigned long long *row_counter;  // 8 bytes of device scratch
@@ -80,8 +81,9 @@ int launch_reservoir(const ReservoirLaunch &l, cudaStream_t stream);
 
 // ---- K4: gather + count + top-k
 struct QueryLaunch {
-  const uint32_t *qkeys;     // [L][q_ld]
+  const uint32_t *qkeys;     // [L][q_ld], or [nq][L] when qkeys_rowmajor
   int64_t q_ld, nq;
+  bool qkeys_rowmajor;
   const int32_t *ids;        // index: [L][n]
   const uint32_t *starts;    // index: [L][2^rb + 1]
   int64_t n;

@@ -37,6 +37,7 @@ constexpr int kQBlockThreads = 256;
 struct QArgs {
   const uint32_t *qkeys;
   int64_t q_ld, nq;
+  bool q_rm;
   const int32_t *ids;
   const uint32_t *starts;
   int64_t n;
@@ -54,6 +55,7 @@ struct QArgs {
 };
 
 struct WarpGroup {
+  static constexpr bool kIsWarp = true;
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
   __device__ __forceinline__ int size() const { return 32; }
   __device__ __forceinline__ void sync() const { __syncwarp(); }
@@ -61,13 +63,14 @@ struct WarpGroup {
 };
 
 struct BlockGroup {
+  static constexpr bool kIsWarp = false;
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int size() const { return blockDim.x; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
   __device__ __forceinline__ bool leader_warp() const { return threadIdx.x < 32; }
 };
 
-// shared layout of one group: [tab][pre L+1][sb L][hist 256][sel kp][misc 8]
+// shared layout of one group: [tab][pre L+1][sb L][hist 256][sel kp][misc 8 + 32]
 struct Region {
   uint32_t *tab, *pre, *sb, *hist, *sel, *misc;
 };
@@ -95,7 +98,7 @@ __device__ __forceinline__ uint32_t ilog2_pow2(uint32_t x) { return 31u - __clz(
 template <class G>
 __device__ uint32_t gather_ranges(const G &g, const QArgs &a, const Region &r, int64_t q) {
   for (uint32_t t = g.rank(); t < a.L; t += g.size()) {
-    const uint32_t key = a.qkeys[static_cast<int64_t>(t) * a.q_ld + q];
+    const uint32_t key = a.q_rm ? a.qkeys[q * a.L + t] : a.qkeys[static_cast<int64_t>(t) * a.q_ld + q];
     uint32_t s = 0, c = 0;
     if (key < a.T) {
       const uint32_t *st = a.starts + static_cast<int64_t>(t) * (static_cast<int64_t>(a.T) + 1);
@@ -142,6 +145,99 @@ __device__ void write_empty(const G &g, const QArgs &a, int64_t q) {
   }
 }
 
+// Ordered in-place compaction of the non-empty table entries into their sort
+// keys tab[0..E).  Writes never pass the read frontier: an entry's rank among
+// the non-empty entries is at most its index, and every round's reads finish
+// before its writes.  `scratch` holds one word per warp of the group.
+template <class G>
+__device__ uint32_t compact_keys(const G &g, uint32_t *tab, uint32_t S, uint32_t *scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (g.size() + 31) >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t out = 0;
+  for (uint32_t base = 0; base < S; base += g.size()) {
+    const uint32_t i = base + g.rank();
+    const uint32_t e = i < S ? tab[i] : 0u;
+    const uint32_t ball = __ballot_sync(kFull, e != 0);
+    uint32_t before = 0, total = __popc(ball);
+    if (nwarps > 1) {
+      if (lane == 0) scratch[warp] = total;
+      g.sync();
+      total = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        const uint32_t c = scratch[w];
+        if (w < warp) before += c;
+        total += c;
+      }
+    }
+    g.sync();
+    if (e) tab[out + before + __popc(ball & lt)] = sort_key(e);
+    out += total;
+    g.sync();
+  }
+  return out;
+}
+
+// Warp bitonic sort, descending, of 32*V keys held V per lane (lane l holds
+// positions l*V .. l*V+V-1).
+template <int V>
+__device__ __forceinline__ void warp_bitonic_desc(uint32_t (&v)[V]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32 * V; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < V) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const int jp = j ^ stride;
+          if (jp > j) {
+            const int i = lane * V + j;
+            const bool desc = (i & size) == 0;
+            const uint32_t x = v[j], y = v[jp];
+            if ((x < y) == desc) {
+              v[j] = y;
+              v[jp] = x;
+            }
+          }
+        }
+      } else {
+        const int lstride = stride / V;
+        const bool lower = (lane & lstride) == 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const uint32_t other = __shfl_xor_sync(kFull, v[j], lstride);
+          const int lo_i = (lower ? lane : (lane ^ lstride)) * V + j;
+          const bool desc = (lo_i & size) == 0;
+          const uint32_t hi = max(v[j], other), lo = min(v[j], other);
+          v[j] = (lower == desc) ? hi : lo;
+        }
+      }
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void warp_sort_and_write(const QArgs &a, const uint32_t *sel, uint32_t nsel, int64_t q) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const uint32_t i = lane * V + j;
+    v[j] = i < nsel ? sel[i] : 0u;
+  }
+  warp_bitonic_desc<V>(v);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = lane * V + j;
+    if (i < a.k) {
+      const uint32_t key = v[j];
+      a.out_ids[q * a.k + i] = key ? static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)) : -1;
+      a.out_counts[q * a.k + i] = key ? static_cast<int32_t>((key >> 24) + 1u) : 0;
+    }
+  }
+}
+
 // Phases B and C for a query whose M candidates fit a table of S words.
 template <class G>
 __device__ void count_and_select(const G &g, const QArgs &a, const Region &r, int64_t q, uint32_t M) {
@@ -151,15 +247,13 @@ __device__ void count_and_select(const G &g, const QArgs &a, const Region &r, in
   for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
   g.sync();
 
-  // ---- count (COUNTFREQUENCY)
+  // ---- count (COUNTFREQUENCY): candidate idx of table t is pre[t] <= idx < pre[t+1];
+  // each thread's idx only grows, so a forward cursor finds t
   const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
+  uint32_t t = 0;
   for (uint32_t idx = g.rank(); idx < M; idx += g.size()) {
-    uint32_t lo = 0, hi = a.L;  // largest t with pre[t] <= idx
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (r.pre[mid] <= idx) lo = mid; else hi = mid;
-    }
-    const int32_t id = a.ids[static_cast<int64_t>(lo) * a.n + r.sb[lo] + (idx - r.pre[lo])];
+    while (r.pre[t + 1] <= idx) ++t;
+    const int32_t id = a.ids[static_cast<int64_t>(t) * a.n + r.sb[t] + (idx - r.pre[t])];
     if (id == excl) continue;
     const uint32_t tag = (static_cast<uint32_t>(id) + 1u) << 8;
     uint32_t h = (static_cast<uint32_t>(id) * 0x9E3779B1u) >> (32 - lg);
@@ -178,51 +272,50 @@ __device__ void count_and_select(const G &g, const QArgs &a, const Region &r, in
   }
   g.sync();
 
-  // ---- radix select of the k-th largest sort key (SORTBYVALUE, top k)
-  uint32_t *misc = r.misc;  // [0]=prefix [1]=pmask [2]=need [3]=done [4]=nsel
-  if (g.rank() == 0) {
-    misc[0] = 0;
-    misc[1] = 0;
-    misc[2] = static_cast<uint32_t>(a.k);
-    misc[3] = 0;
-    misc[4] = 0;
-  }
-  for (int pass = 0; pass < 4; ++pass) {
-    const int shift = 24 - 8 * pass;
-    for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
-    g.sync();
-    const uint32_t prefix = misc[0], pmask = misc[1];
-    for (uint32_t i = g.rank(); i < S; i += g.size()) {
-      const uint32_t e = r.tab[i];
-      if (e) {
-        const uint32_t key = sort_key(e);
+  // ---- sort keys of the distinct candidates, packed to the front of tab
+  uint32_t *misc = r.misc;  // [0]=prefix [1]=pmask [2]=need [3]=done [4]=nsel [8..]=per-warp scratch
+  const uint32_t E = compact_keys(g, r.tab, S, misc + 8);
+  const uint32_t *keys = r.tab;
+
+  // ---- radix select of the k-th largest key (SORTBYVALUE, top k), 8-bit digits from the top
+  uint32_t thr = 1;  // E <= k: every key is selected
+  if (E > static_cast<uint32_t>(a.k)) {
+    if (g.rank() == 0) {
+      misc[0] = 0;
+      misc[1] = 0;
+      misc[2] = static_cast<uint32_t>(a.k);
+      misc[3] = 0;
+    }
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+      for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
+      g.sync();
+      const uint32_t prefix = misc[0], pmask = misc[1];
+      for (uint32_t i = g.rank(); i < E; i += g.size()) {
+        const uint32_t key = keys[i];
         if ((key & pmask) == prefix) atomicAdd(&r.hist[(key >> shift) & 0xFFu], 1u);
       }
-    }
-    g.sync();
-    if (g.leader_warp()) {
-      const int lane = threadIdx.x & 31;
-      uint32_t s = 0;
+      g.sync();
+      if (g.leader_warp()) {
+        const int lane = threadIdx.x & 31;
+        uint32_t s = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) s += r.hist[lane * 8 + i];
-      uint32_t suf = s;
+        for (int i = 0; i < 8; ++i) s += r.hist[lane * 8 + i];
+        uint32_t suf = s;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t x = __shfl_down_sync(kFull, suf, o);
-        if (lane + o < 32) suf += x;
-      }
-      const uint32_t total = __shfl_sync(kFull, suf, 0);
-      const uint32_t need = misc[2];
-      if (pass == 0 && total <= need) {
-        if (lane == 0) misc[3] = 1;
-      } else {
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t x = __shfl_down_sync(kFull, suf, o);
+          if (lane + o < 32) suf += x;
+        }
+        const uint32_t need = misc[2];
         const uint32_t ball = __ballot_sync(kFull, suf >= need);
         const int ln = 31 - __clz(ball);
         if (lane == ln) {
           uint32_t cum = suf - s;
           int d = lane * 8;
+          uint32_t c = 0;
           for (int i = 7; i >= 0; --i) {
-            const uint32_t c = r.hist[lane * 8 + i];
+            c = r.hist[lane * 8 + i];
             if (cum + c >= need) {
               d = lane * 8 + i;
               break;
@@ -232,27 +325,35 @@ __device__ void count_and_select(const G &g, const QArgs &a, const Region &r, in
           misc[2] = need - cum;
           misc[0] = prefix | (static_cast<uint32_t>(d) << shift);
           misc[1] = pmask | (0xFFu << shift);
+          if (c == need - cum) misc[3] = 1;  // the whole digit bucket is taken: lower digits do not matter
         }
       }
+      g.sync();
+      if (misc[3]) break;
     }
-    g.sync();
-    if (misc[3]) break;
+    thr = misc[0];
   }
-  const uint32_t thr = misc[3] ? 1u : misc[0];
 
-  // ---- collect and sort the winners
-  for (uint32_t i = g.rank(); i < S; i += g.size()) {
-    const uint32_t e = r.tab[i];
-    if (e) {
-      const uint32_t key = sort_key(e);
-      if (key >= thr) {
-        const uint32_t pos = atomicAdd(&misc[4], 1u);
-        if (pos < a.kp) r.sel[pos] = key;  // exactly min(k, distinct) keys reach here
-      }
+  // ---- collect the winners (exactly min(k, E) keys are >= thr)
+  if (g.rank() == 0) misc[4] = 0;
+  g.sync();
+  for (uint32_t i = g.rank(); i < E; i += g.size()) {
+    const uint32_t key = keys[i];
+    if (key >= thr) {
+      const uint32_t pos = atomicAdd(&misc[4], 1u);
+      if (pos < a.kp) r.sel[pos] = key;
     }
   }
   g.sync();
   const uint32_t nsel = misc[4] < a.kp ? misc[4] : a.kp;
+  if (G::kIsWarp) {
+    if (a.kp <= 32) warp_sort_and_write<1>(a, r.sel, nsel, q);
+    else if (a.kp <= 64) warp_sort_and_write<2>(a, r.sel, nsel, q);
+    else if (a.kp <= 128) warp_sort_and_write<4>(a, r.sel, nsel, q);
+    else warp_sort_and_write<8>(a, r.sel, nsel, q);
+    g.sync();
+    return;
+  }
   for (uint32_t i = nsel + g.rank(); i < a.kp; i += g.size()) r.sel[i] = 0;
   g.sync();
   for (uint32_t size = 2; size <= a.kp; size <<= 1) {
@@ -323,7 +424,7 @@ uint32_t next_pow2(uint32_t x) {
 }
 
 uint32_t region_words(const QArgs &a) {
-  return a.table_words + ((a.L + 1 + 3) & ~3u) + ((a.L + 3) & ~3u) + 256 + a.kp + 8;
+  return a.table_words + ((a.L + 1 + 3) & ~3u) + ((a.L + 3) & ~3u) + 256 + a.kp + 40;
 }
 
 }  // namespace
@@ -334,6 +435,7 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
   a.qkeys = l.qkeys;
   a.q_ld = l.q_ld;
   a.nq = l.nq;
+  a.q_rm = l.qkeys_rowmajor;
   a.ids = l.ids;
   a.starts = l.starts;
   a.n = l.n;

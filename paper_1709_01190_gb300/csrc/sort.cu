@@ -12,11 +12,12 @@
 //   scatter : per (table, tile) stable ranking -- warps take consecutive
 //             32-element rounds, __match_any_sync ranks equal digits within
 //             a round, per-warp running counts and a per-digit prefix over
-//             warps keep the tile's element order -- and a scatter to
-//             scan offset + rank.
+//             warps keep the tile's element order -- a stable local sort of
+//             the tile by digit in shared memory, and coalesced writes of each
+//             digit run to scan offset + position in the run.
 // Finally the bucket starts: starts[t][b] = number of addresses < b in table
-// t, for b in [0, 2^rb]; each key change writes the starts of the skipped
-// buckets, a warp at a time.
+// t, for b in [0, 2^rb]; each key change writes the starts of the buckets it
+// skips: a short run by its own thread, a long run by the whole warp.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -27,8 +28,8 @@ namespace flash {
 namespace {
 
 constexpr int kSortWarps = 8;
-constexpr int kSortItems = 8;
-constexpr int kMaxBinsSort = 257;
+constexpr int kTile = 4096;         // elements per (table, tile) block, histogram and scatter
+constexpr int kMaxBinsSort = 257;   // 8-bit digit + the sentinel value
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct PassArgs {
@@ -104,66 +105,128 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *hist, int64_
   }
 }
 
+// Scatter of one (table, tile) block: rank, sort the tile locally by digit
+// in shared memory (stable), then write every digit run of the tile to its
+// global place with consecutive threads on consecutive addresses.
 template <bool FIRST>
 __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const uint32_t *keys_in, const int32_t *ids_in,
-                                                                       int64_t n, PassArgs p, uint32_t tile, int64_t tiles,
+                                                                       int64_t n, PassArgs p, int64_t tiles,
                                                                        const uint32_t *offs, uint32_t *keys_out,
-                                                                       int32_t *ids_out) {
-  __shared__ uint32_t run[kMaxBinsSort + 7];
-  __shared__ uint32_t wcnt[kSortWarps][kMaxBinsSort + 7];
-  __shared__ uint32_t wpref[kSortWarps][kMaxBinsSort + 7];
+                                                                       int32_t *ids_out, int nb_pad) {
+  extern __shared__ uint32_t sm[];
+  uint32_t *skey = sm;                                          // [kTile] keys, tile order
+  int32_t *sid = reinterpret_cast<int32_t *>(skey + kTile);     // [kTile] ids (not FIRST)
+  uint32_t *wcnt = reinterpret_cast<uint32_t *>(sid + (FIRST ? 0 : kTile));  // [kSortWarps][nb_pad]
+  uint32_t *wpref = wcnt + kSortWarps * nb_pad;                 // [kSortWarps][nb_pad]
+  uint32_t *toff = wpref + kSortWarps * nb_pad;                 // [nb_pad] digit offset inside the tile
+  uint32_t *goff = toff + nb_pad;                               // [nb_pad] digit offset in the table
+  uint16_t *perm = reinterpret_cast<uint16_t *>(goff + nb_pad); // [kTile] tile index in digit order
   const uint32_t t = blockIdx.y;
   const int64_t ti = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t seg = static_cast<int64_t>(t) * n;
+  const int64_t a = ti * kTile;
+  const int cnt = static_cast<int>(min(n - a, static_cast<int64_t>(kTile)));
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int d = threadIdx.x; d < p.nbins; d += blockDim.x)
-    run[d] = offs[(static_cast<int64_t>(t) * p.nbins + d) * tiles + ti];
-  const int64_t a = ti * tile, b = min(n, a + static_cast<int64_t>(tile));
-  constexpr int kChunk = kSortWarps * 32 * kSortItems;
-  for (int64_t cb = a; cb < b; cb += kChunk) {
-    for (int d = lane; d < p.nbins; d += 32) wcnt[warp][d] = 0;
+  uint32_t *my_cnt = wcnt + warp * nb_pad;
+  for (int d = threadIdx.x; d < p.nbins; d += blockDim.x) goff[d] = offs[(static_cast<int64_t>(t) * p.nbins + d) * tiles + ti];
+  for (int d = lane; d < p.nbins; d += 32) my_cnt[d] = 0;
+  __syncwarp();
+
+  // 1. load (coalesced) and rank: warp w holds tile elements [w*W, (w+1)*W) in 32-element rounds
+  constexpr int kPerWarp = kTile / kSortWarps;
+  constexpr int kRounds = kPerWarp / 32;
+  uint32_t dr[kRounds];  // digit << 16 | rank among the warp's equal digits
+  uint32_t kk[kRounds];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int e = warp * kPerWarp + r * 32 + lane;
+    kk[r] = e < cnt ? __ldcs(keys_in + seg + a + e) : 0u;
+  }
+  if (!FIRST) {
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const int e = warp * kPerWarp + r * 32 + lane;
+      if (e < cnt) sid[e] = __ldcs(ids_in + seg + a + e);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int e = warp * kPerWarp + r * 32 + lane;
+    const bool valid = e < cnt;
+    if (valid) skey[e] = kk[r];
+    const uint32_t d = valid ? digit_of(kk[r], p) : 0xFFFFu;
+    const uint32_t peers = __match_any_sync(kFull, d);
+    const uint32_t lower = peers & lt_mask;
+    const uint32_t before = valid ? my_cnt[d] : 0u;
     __syncwarp();
-    uint32_t kk[kSortItems], dd[kSortItems], rr[kSortItems];
-    int32_t vv[kSortItems];
+    if (valid && lower == 0) my_cnt[d] = before + __popc(peers);
+    __syncwarp();
+    dr[r] = (d << 16) | (before + __popc(lower));
+  }
+  __syncthreads();
+
+  // 2. per digit: warp prefixes and the tile count; then offsets of the digits inside the tile
+  for (int d = threadIdx.x; d < p.nbins; d += blockDim.x) {
+    uint32_t acc = 0;
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-      const int64_t e = cb + static_cast<int64_t>(warp) * 32 * kSortItems + r * 32 + lane;
-      const bool valid = e < b;
-      const uint32_t key = valid ? __ldcs(keys_in + seg + e) : 0u;
-      const int32_t val = FIRST ? static_cast<int32_t>(e) : (valid ? __ldcs(ids_in + seg + e) : 0);
-      const uint32_t d = valid ? digit_of(key, p) : 0xFFFFu;
-      const uint32_t peers = __match_any_sync(kFull, d);
-      const uint32_t lower = peers & lt_mask;
-      const uint32_t before = valid ? wcnt[warp][d] : 0u;
-      __syncwarp();
-      if (valid && lower == 0) wcnt[warp][d] = before + __popc(peers);
-      __syncwarp();
-      kk[r] = key;
-      vv[r] = val;
-      dd[r] = d;
-      rr[r] = before + __popc(lower);
+    for (int w = 0; w < kSortWarps; ++w) {
+      wpref[w * nb_pad + d] = acc;
+      acc += wcnt[w * nb_pad + d];
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < p.nbins; d += blockDim.x) {
-      uint32_t acc = run[d];
-#pragma unroll
-      for (int w = 0; w < kSortWarps; ++w) {
-        wpref[w][d] = acc;
-        acc += wcnt[w][d];
-      }
-      run[d] = acc;
+    toff[d] = acc;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int per = (p.nbins + 31) / 32;
+    uint32_t sum = 0;
+    for (int i = 0; i < per; ++i) {
+      const int d = lane * per + i;
+      if (d < p.nbins) sum += toff[d];
     }
-    __syncthreads();
+    uint32_t inc = sum;
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-      if (dd[r] != 0xFFFFu) {
-        const int64_t dest = seg + wpref[warp][dd[r]] + rr[r];
-        keys_out[dest] = kk[r];
-        ids_out[dest] = vv[r];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += x;
+    }
+    uint32_t run = inc - sum;
+    for (int i = 0; i < per; ++i) {
+      const int d = lane * per + i;
+      if (d < p.nbins) {
+        const uint32_t c = toff[d];
+        toff[d] = run;
+        run += c;
       }
     }
   }
+  __syncthreads();
+
+  // 3. stable local order by digit
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const uint32_t d = dr[r] >> 16;
+    if (d != 0xFFFFu) {
+      const int e = warp * kPerWarp + r * 32 + lane;
+      perm[toff[d] + wpref[warp * nb_pad + d] + (dr[r] & 0xFFFFu)] = static_cast<uint16_t>(e);
+    }
+  }
+  __syncthreads();
+
+  // 4. coalesced writes of the digit runs
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int e = perm[i];
+    const uint32_t key = skey[e];
+    const uint32_t d = digit_of(key, p);
+    const int64_t dest = seg + goff[d] + (static_cast<uint32_t>(i) - toff[d]);
+    keys_out[dest] = key;
+    ids_out[dest] = FIRST ? static_cast<int32_t>(a + e) : sid[e];
+  }
+}
+
+size_t scatter_smem_bytes(bool first, int nb_pad) {
+  return sizeof(uint32_t) * (kTile + (first ? 0 : kTile) + (2 * kSortWarps + 2) * static_cast<size_t>(nb_pad)) +
+         sizeof(uint16_t) * kTile;
 }
 
 __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skeys, int64_t n, uint32_t T,
@@ -182,6 +245,12 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
       const int64_t kc = i < n ? static_cast<int64_t>(seg[i]) : static_cast<int64_t>(T) + 1;
       lo = kp + 1;
       hi = kc < static_cast<int64_t>(T) ? kc : static_cast<int64_t>(T);
+    }
+    // short gaps (the common case: about n / 2^rb addresses per bucket) by the thread itself
+    if (lo <= hi && hi - lo < 8) {
+      for (int64_t bkt = lo; bkt <= hi; ++bkt) st[bkt] = static_cast<uint32_t>(i);
+      lo = 1;
+      hi = 0;
     }
     uint32_t m = __ballot_sync(kFull, lo <= hi);
     while (m) {
@@ -209,7 +278,7 @@ SortPlan make_sort_plan(uint32_t range_bits, int64_t n, uint32_t L) {
     p.nbins[i] = (1 << p.bits[i]) + (i == p.passes - 1 ? 1 : 0);
     if (p.nbins[i] > maxb) maxb = p.nbins[i];
   }
-  p.tile = n >= (4LL << 20) ? 16384u : 8192u;
+  p.tile = kTile;
   p.tiles = n > 0 ? (n + p.tile - 1) / p.tile : 0;
   p.hist_words = static_cast<int64_t>(L) * maxb * (p.tiles > 0 ? p.tiles : 1);
   return p;
@@ -230,12 +299,12 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
     int32_t *vout = to_final ? s.ids_out : s.tmp_ids;
     radix_hist_kernel<<<grid, 256, 0, stream>>>(kin, s.n, pa, plan.tile, plan.tiles, s.hist);
     radix_scan_kernel<<<s.L, 1024, 0, stream>>>(s.hist, static_cast<int64_t>(pa.nbins) * plan.tiles);
-    if (pass == 0)
-      radix_scatter_kernel<true><<<grid, kSortWarps * 32, 0, stream>>>(kin, vin, s.n, pa, plan.tile, plan.tiles,
-                                                                       s.hist, kout, vout);
-    else
-      radix_scatter_kernel<false><<<grid, kSortWarps * 32, 0, stream>>>(kin, vin, s.n, pa, plan.tile, plan.tiles,
-                                                                        s.hist, kout, vout);
+    const int nb_pad = (pa.nbins + 3) & ~3;
+    const size_t smem = scatter_smem_bytes(pass == 0, nb_pad);
+    auto kern = pass == 0 ? radix_scatter_kernel<true> : radix_scatter_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+      return FLASH_ECUDA;
+    kern<<<grid, kSortWarps * 32, smem, stream>>>(kin, vin, s.n, pa, plan.tiles, s.hist, kout, vout, nb_pad);
     count_launches(3);
     kin = kout;
     vin = vout;

@@ -125,6 +125,10 @@ BUILD_CASES = [
     ("tiny_plain", 4_000, dict(range_bits=9, R=200, L=4)),  # R above every occupancy
     ("url_like_batched", 30_000, dict(range_bits=12)),   # Zipf heavy buckets, R = 128
     ("kdd12_like", 40_000, dict(range_bits=13, L=32)),
+    ("kdd12_like", 30_000, dict(range_bits=20, L=4, R=2)),          # two 10-bit digit passes
+    ("url_like_batched", 20_000, dict(range_bits=21, L=2, R=4, K=2)),  # three passes
+    ("tiny_plain", 5_000, dict(range_bits=10, R=4)),                 # one pass
+    ("tiny_plain", 5_000, dict(range_bits=1, R=64, L=3)),            # two buckets: m >> R everywhere
 ]
 
 
