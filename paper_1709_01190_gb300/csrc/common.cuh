@@ -73,6 +73,37 @@ __device__ __forceinline__ uint32_t reservoir_draw(uint64_t bucket_key, uint32_t
   return static_cast<uint32_t>(((u >> 32) * (static_cast<uint64_t>(i) + 1ULL)) >> 32);
 }
 
+// ------------------------------------------------ L2 eviction priorities
+// Per-access hints (no device setting changes): data that a later phase reads
+// at random (bucket starts, grouped ids) is kept with evict_last; streams read
+// or written once go with evict_first.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_l2(const uint32_t *ptr, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_l2(const int32_t *ptr, uint64_t pol) {
+  int32_t v;
+  asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_l2(uint32_t *ptr, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_l2(int32_t *ptr, int32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+}
+
 inline unsigned div_up(uint64_t a, uint64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
 
 int num_sms();

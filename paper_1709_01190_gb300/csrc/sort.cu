@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *hist, int64_
 // Scatter of one (table, tile) block: rank, sort the tile locally by digit
 // in shared memory (stable), then write every digit run of the tile to its
 // global place with consecutive threads on consecutive addresses.
-template <bool FIRST>
+template <bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const uint32_t *keys_in, const int32_t *ids_in,
                                                                        int64_t n, PassArgs p, int64_t tiles,
                                                                        const uint32_t *offs, uint32_t *keys_out,
@@ -219,8 +219,14 @@ __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const ui
     const uint32_t key = skey[e];
     const uint32_t d = digit_of(key, p);
     const int64_t dest = seg + goff[d] + (static_cast<uint32_t>(i) - toff[d]);
-    keys_out[dest] = key;
-    ids_out[dest] = FIRST ? static_cast<int32_t>(a + e) : sid[e];
+    const int32_t id = FIRST ? static_cast<int32_t>(a + e) : sid[e];
+    if (LAST) {  // final order: the ids stay in L2 for the query phase, the keys only feed the starts
+      st_l2(ids_out + dest, id, l2_policy_keep());
+      st_l2(keys_out + dest, key, l2_policy_stream());
+    } else {
+      keys_out[dest] = key;
+      ids_out[dest] = id;
+    }
   }
 }
 
@@ -236,6 +242,7 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
   uint32_t *st = starts + static_cast<int64_t>(t) * (static_cast<int64_t>(T) + 1);
   const int lane = threadIdx.x & 31;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const uint64_t keep = l2_policy_keep();
   for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base <= n;
        base += stride) {
     const int64_t i = base + lane;
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
     }
     // short gaps (the common case: about n / 2^rb addresses per bucket) by the thread itself
     if (lo <= hi && hi - lo < 8) {
-      for (int64_t bkt = lo; bkt <= hi; ++bkt) st[bkt] = static_cast<uint32_t>(i);
+      for (int64_t bkt = lo; bkt <= hi; ++bkt) st_l2(st + bkt, static_cast<uint32_t>(i), keep);
       lo = 1;
       hi = 0;
     }
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
       m &= m - 1;
       const int64_t glo = __shfl_sync(kFull, lo, src), ghi = __shfl_sync(kFull, hi, src);
       const uint32_t gi = static_cast<uint32_t>(__shfl_sync(kFull, i, src));
-      for (int64_t bkt = glo + lane; bkt <= ghi; bkt += 32) st[bkt] = gi;
+      for (int64_t bkt = glo + lane; bkt <= ghi; bkt += 32) st_l2(st + bkt, gi, keep);
     }
   }
 }
@@ -301,7 +308,9 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
     radix_scan_kernel<<<s.L, 1024, 0, stream>>>(s.hist, static_cast<int64_t>(pa.nbins) * plan.tiles);
     const int nb_pad = (pa.nbins + 3) & ~3;
     const size_t smem = scatter_smem_bytes(pass == 0, nb_pad);
-    auto kern = pass == 0 ? radix_scatter_kernel<true> : radix_scatter_kernel<false>;
+    const bool last = pass == plan.passes - 1;
+    auto kern = pass == 0 ? (last ? radix_scatter_kernel<true, true> : radix_scatter_kernel<true, false>)
+                          : (last ? radix_scatter_kernel<false, true> : radix_scatter_kernel<false, false>);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
       return FLASH_ECUDA;
     kern<<<grid, kSortWarps * 32, smem, stream>>>(kin, vin, s.n, pa, plan.tiles, s.hist, kout, vout, nb_pad);
