@@ -60,16 +60,6 @@ __device__ __forceinline__ void bin_and_offset(uint32_t c, const Seeds &s, uint3
   off = static_cast<uint32_t>(p);
 }
 
-// Same value as bin_and_offset in fewer instructions: with a1 = a1_hi*2^32 + a1_lo,
-// (a1*c + b1) >> 32 = ((a1_lo*c + b1) >> 32) + a1_hi*c  (mod 2^32).
-__device__ __forceinline__ void bin_and_offset_fast(uint32_t c, uint32_t a1_lo, uint32_t a1_hi, uint64_t b1,
-                                                    uint32_t B, uint32_t &bin, uint32_t &off) {
-  const uint64_t t = static_cast<uint64_t>(a1_lo) * c + b1;
-  const uint32_t pi = static_cast<uint32_t>(t >> 32) + a1_hi * c;
-  bin = __umulhi(pi, B);
-  off = pi * B;
-}
-
 __device__ __forceinline__ void insert_dense(uint32_t c, const DophParams &a, uint32_t *bins, uint32_t *mask) {
   if (c >= a.dim_u32) {
     raise_error(a.err, FLASH_DEVERR_COL_RANGE);

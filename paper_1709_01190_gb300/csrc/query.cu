@@ -404,7 +404,7 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
   }
   g.sync();
   const uint32_t nsel = misc[5] < a.kp ? misc[5] : a.kp;
-  if (G::kIsWarp) {
+  if constexpr (G::kIsWarp) {
     if (nsel <= 32) warp_sort_and_write<1>(a, r.sel, nsel, q);
     else if (nsel <= 64) warp_sort_and_write<2>(a, r.sel, nsel, q);
     else if (nsel <= 128) warp_sort_and_write<4>(a, r.sel, nsel, q);
