@@ -410,30 +410,30 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
     else if (nsel <= 128) warp_sort_and_write<4>(a, r.sel, nsel, q);
     else warp_sort_and_write<8>(a, r.sel, nsel, q);
     g.sync();
-    return;
-  }
-  for (uint32_t i = nsel + g.rank(); i < a.kp; i += g.size()) r.sel[i] = 0;
-  g.sync();
-  for (uint32_t size = 2; size <= a.kp; size <<= 1) {
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      for (uint32_t i = g.rank(); i < a.kp / 2; i += g.size()) {
-        const uint32_t lo = (i / stride) * stride * 2 + (i % stride), hi = lo + stride;
-        const bool desc = (lo & size) == 0;
-        const uint32_t x = r.sel[lo], y = r.sel[hi];
-        if ((x < y) == desc) {
-          r.sel[lo] = y;
-          r.sel[hi] = x;
+  } else {
+    for (uint32_t i = nsel + g.rank(); i < a.kp; i += g.size()) r.sel[i] = 0;
+    g.sync();
+    for (uint32_t size = 2; size <= a.kp; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t i = g.rank(); i < a.kp / 2; i += g.size()) {
+          const uint32_t lo = (i / stride) * stride * 2 + (i % stride), hi = lo + stride;
+          const bool desc = (lo & size) == 0;
+          const uint32_t x = r.sel[lo], y = r.sel[hi];
+          if ((x < y) == desc) {
+            r.sel[lo] = y;
+            r.sel[hi] = x;
+          }
         }
+        g.sync();
       }
-      g.sync();
     }
+    for (int j = g.rank(); j < a.k; j += g.size()) {
+      const uint32_t key = r.sel[j];
+      __stcs(a.out_ids + q * a.k + j, key ? static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)) : -1);
+      __stcs(a.out_counts + q * a.k + j, key ? static_cast<int32_t>((key >> 24) + 1u) : 0);
+    }
+    g.sync();
   }
-  for (int j = g.rank(); j < a.k; j += g.size()) {
-    const uint32_t key = r.sel[j];
-    __stcs(a.out_ids + q * a.k + j, key ? static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)) : -1);
-    __stcs(a.out_counts + q * a.k + j, key ? static_cast<int32_t>((key >> 24) + 1u) : 0);
-  }
-  g.sync();
 }
 
 __device__ __forceinline__ unsigned long long claim_query(const QArgs &a) {
