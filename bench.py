@@ -22,6 +22,7 @@ independent replica with its own data seed (no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement (url-like index)")
+    ap.add_argument("--no-tune", action="store_true", help="skip autotuning of the launch knobs")
     return ap.parse_args()
 
 
@@ -159,6 +162,116 @@ def cpu_baseline(w, csr, target_s: float) -> dict:
                       f"query of those rows, plain single-threaded C oracle, {t:.1f} s"}
 
 
+def serving_measurement(fl, seconds_per_load: float = 1.5) -> dict:
+    """Served p50/p99 and queries/s on the url-like index (resident), requests of U[1, 4096] query rows."""
+    import threading
+    import torch
+    from paper_1709_01190_gb300 import serve, synth
+    w = synth.WORKLOADS["serving_url"]
+    p = w.params
+    params = fl.FlashParams(p.K, p.L, p.R, p.range_bits, p.seed)
+    data = synth.generate(w.data)
+    ix = fl.flash_build(params, fl.DeviceCSR.from_host(data))
+    torch.cuda.synchronize()
+    dim = data.dim
+    del data
+    qc = synth.generate(w.query_data)
+    rng = np.random.default_rng(5)
+    reqs, r0 = [], 0
+    while True:
+        s = int(rng.integers(1, 4097))
+        if r0 + s > qc.n_rows:
+            break
+        sub = qc.slice(r0, r0 + s)
+        reqs.append((sub.row_ptr, sub.col))
+        r0 += s
+    mean_rows = float(np.mean([rp.shape[0] - 1 for rp, _ in reqs]))
+    k = w.k
+    out = {"workload": w.name, "index_rows": int(ix.n_rows), "k": k, "slots": 4, "mem_budget_bytes": 8 << 30}
+
+    # one launch over all 1,000,000 query rows (the batched form), device-timed
+    d_q = fl.DeviceCSR.from_host(qc)
+    ids = torch.empty((qc.n_rows, k), dtype=torch.int32, device="cuda")
+    cnt = torch.empty_like(ids)
+    fl.flash_query(ix, d_q, k, None, ids, cnt)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fl.flash_query(ix, d_q, k, None, ids, cnt)
+    b.record()
+    torch.cuda.synchronize()
+    out["one_launch_queries_per_s"] = qc.n_rows / (a.elapsed_time(b) / 1e3)
+    del d_q, ids, cnt
+
+    def server():
+        return serve.Server(serve.CudaBackend(ix, k, dim, n_slots=4), mem_budget=8 << 30, max_batch_rows=16384)
+
+    # saturated (closed loop: everything queued at once)
+    srv = server()
+    for t in [srv.submit(*r) for r in reqs[:8]]:
+        t.wait(120)
+    srv.close()
+    srv = server()
+    n_sat = min(len(reqs), 160)
+    t0 = time.perf_counter()
+    ts = [srv.submit(*r) for r in reqs[:n_sat]]
+    for t in ts:
+        t.wait(300)
+    sat_s = time.perf_counter() - t0
+    srv.close()
+    sat_rows = sum(r[0].shape[0] - 1 for r in reqs[:n_sat])
+    out["saturated_queries_per_s"] = sat_rows / sat_s
+    out["saturated_batches"] = srv.stats()["batches"]
+
+    # plain path: one request at a time, one stream, copy in / query / copy out / wait
+    n_plain = min(len(reqs), 40)
+    serve.plain_serve(ix, k, reqs[:2], dim)
+    t0 = time.perf_counter()
+    serve.plain_serve(ix, k, reqs[:n_plain], dim)
+    plain_s = time.perf_counter() - t0
+    out["plain_queries_per_s"] = sum(r[0].shape[0] - 1 for r in reqs[:n_plain]) / plain_s
+
+    # open loop: Poisson arrivals at fractions of the saturated rate
+    loads = {}
+    pos = n_sat
+    for load in (0.5, 0.8):
+        rate = load * out["saturated_queries_per_s"] / mean_rows  # requests per second
+        srv = server()
+        stop = time.perf_counter() + seconds_per_load
+        arng = np.random.default_rng(int(load * 100))
+        sent = []
+
+        def gen():
+            nonlocal pos
+            t_next = time.perf_counter()
+            while time.perf_counter() < stop and pos < len(reqs):
+                t_next += arng.exponential(1.0 / rate)
+                dt = t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                sent.append(srv.submit(*reqs[pos]))
+                pos += 1
+
+        th = threading.Thread(target=gen)
+        t0 = time.perf_counter()
+        th.start()
+        th.join()
+        for t in sent:
+            t.wait(300)
+        wall = time.perf_counter() - t0
+        srv.close()
+        st = srv.stats()
+        loads[str(load)] = {"offered_queries_per_s": load * out["saturated_queries_per_s"],
+                            "served_queries_per_s": st["rows"] / wall, "p50_ms": st.get("p50_ms"),
+                            "p99_ms": st.get("p99_ms"), "requests": st["requests"], "batches": st["batches"]}
+        if pos >= len(reqs):
+            pos = n_sat
+    out["poisson"] = loads
+    out["mean_request_rows"] = mean_rows
+    ix.free()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -227,6 +340,14 @@ def main():
     def step():
         fl.flash_knn_graph(params, dev, k, ids, cnt, stream)
 
+    tuned = None
+    if not args.no_tune:
+        from paper_1709_01190_gb300 import tuning
+        os.environ.setdefault("FLASH_TUNING_CACHE", os.path.join(tempfile.gettempdir(), "flash_tuning_bench.json"))
+        key = tuning.shape_key("graph", params, n, nnz, k)
+        best, _ = tuning.autotune(step, key=key, reps=2)
+        tuned = dataclasses.asdict(best)
+
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -283,27 +404,43 @@ def main():
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    graph_ms = None
+    try:
+        from paper_1709_01190_gb300 import tuning as _t
+        g = _t.GraphedKnnGraph(params, dev, k, ids, cnt)
+        graph_ms = timed(g.replay, max(args.steps, 5))
+        del g
+    except Exception as e:  # report, do not fail the bench
+        graph_ms = f"capture failed: {e}"
+
     keys_ms = timed(lambda: fl.flash_keys(params, dev, keys_out, stream), max(args.steps, 5))
     hash_ms = timed(lambda: fl.flash_hash(params, dev, hashes_out, stream), max(args.steps, 5))
-    del keys_out, hashes_out
     in_bytes = 8 * (n + 1) + 4 * nnz
-    keys_bytes = in_bytes + 4 * p.L * n
+    keys_bytes = in_bytes + 4 * p.L * n           # flash_keys: one key array
+    phase_bytes = in_bytes + 8 * p.L * n          # graph hash phase: keys table-major + row-major copy
     hash_bytes = in_bytes + 4 * p.K * p.L * n
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     peak, peak_src = (hbm, "measured") if hbm else (6800.0, "fallback")
     hash_phase_ms = acc.get("hash", keys_ms)
-    achieved = keys_bytes / (hash_phase_ms / 1000.0) / 1e9
+    achieved = phase_bytes / (hash_phase_ms / 1000.0) / 1e9
     roofline = {"kernel": "doph_kernel<keys> (hash phase of the graph step)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, torch copy read+write)",
-                "algorithmic_bytes_per_launch": keys_bytes,
-                "bytes_formula": "8(N+1) + 4 nnz + 4 L N", "traffic": None}
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, torch copy read+write; kernel timed "
+                                          "inside the step, burst copy figure)",
+                "algorithmic_bytes_per_launch": phase_bytes,
+                "bytes_formula": "8(N+1) + 4 nnz + 8 L N", "traffic": None,
+                "duration_ms": hash_phase_ms}
     prof = os.path.join(ROOT, "profiles", "doph_keys_webspam_like_traffic.json")
-    if os.path.exists(prof) and not args.rows:
+    if os.path.exists(prof) and not args.rows and args.workload == "webspam_like":
         try:
+            import hashlib
             with open(prof) as fh:
-                roofline["traffic"] = json.load(fh).get("traffic_bytes_per_launch")
+                rec = json.load(fh)
+            fresh = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                        for f, h in rec.get("source_sha256", {}).items())
+            # counters describe the kernel as it was captured: none once it has changed since
+            roofline["traffic"] = rec.get("traffic_bytes_per_launch") if fresh else None
         except (OSError, ValueError):
             pass
     doph = {"GB/s": hash_bytes / (hash_ms / 1000.0) / 1e9, "ms": hash_ms, "bytes": hash_bytes,
@@ -328,6 +465,12 @@ def main():
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * n * k,
                "api": "flash_knn_graph_host (pinned host buffers)"}
 
+    served = None
+    if rank == 0 and world == 1 and not args.no_serve and not args.rows:
+        del dev, keys_out, hashes_out
+        torch.cuda.empty_cache()
+        served = serving_measurement(fl)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, csr, args.cpu_seconds)
@@ -338,7 +481,8 @@ def main():
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded, webspam-shaped; see config)",
                 "config": config_of(w, csr), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "phases_ms": acc, "doph": doph, "reduced": bool(args.rows)}
+                "phases_ms": acc, "doph": doph, "graph_replay_ms_per_step": graph_ms, "tuning": tuned,
+                "served": served, "reduced": bool(args.rows)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -183,6 +183,25 @@ size_t flash_knn_graph_scratch_bytes(const flash_params *p, int64_t n_rows);
 /* Scratch bytes flash_query needs for q_rows query rows. */
 size_t flash_query_scratch_bytes(const flash_params *p, int64_t q_rows);
 
+/* Launch knobs chosen by an autotuner (process-wide; every call reads them
+ * once when it starts).  Zero means the library's automatic choice.
+ *   query_warp_table   : words of the per-warp count table of the query kernel
+ *                        (power of two, 64..8192); queries whose candidates do
+ *                        not fit go to the block-per-query path
+ *   doph_rows_per_grab : rows a warp of the DOPH kernel claims at a time (1..4096)
+ *   doph_order         : 0 = rows in index order, 1 = longest rows first
+ *                        (rows binned by log2 of their length; results are
+ *                        identical, only the schedule changes) */
+typedef struct flash_tuning {
+  uint32_t query_warp_table;
+  uint32_t doph_rows_per_grab;
+  uint32_t doph_order;
+} flash_tuning;
+
+/* Set the knobs (NULL restores the automatic choices); FLASH_EINVAL if out of range. */
+int flash_set_tuning(const flash_tuning *t);
+int flash_get_tuning(flash_tuning *t);
+
 /* Per-phase device timing of the calling thread's flash_knn_graph calls
  * (instrumentation; off by default).  flash_enable_phase_timing(1) makes
  * later calls record a CUDA event on their stream before each phase (hash,

@@ -48,6 +48,7 @@ struct DophParams {
   bool vec_out;
   uint32_t *err;
   unsigned long long *row_counter;
+  const int32_t *order;  // optional processing order of the rows (longest first)
 };
 
 __device__ __forceinline__ void bin_and_offset(uint32_t c, const Seeds &s, uint32_t B, uint32_t &bin,
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) doph_kernel(DophParams
       cend = min(cpos + G, a.n_rows);
       if (lane == 0) claim = atomicAdd(a.row_counter, static_cast<unsigned long long>(G));
     }
-    return cpos++;
+    const int64_t pos = cpos++;
+    return a.order ? static_cast<int64_t>(a.order[pos]) : pos;
   };
   auto bounds = [&](int64_t r, int64_t &st, int64_t &en) {
     st = 0;
@@ -363,7 +365,53 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) doph_kernel(DophParams
   }
 }
 
+// ---- longest-rows-first processing order: rows binned by ceil(log2(nnz + 1))
+__global__ void __launch_bounds__(256) row_class_hist_kernel(const int64_t *row_ptr, int64_t n, uint32_t *hist) {
+  __shared__ uint32_t h[40];
+  if (threadIdx.x < 40) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t m = row_ptr[r + 1] - row_ptr[r];
+    const uint32_t c = m > 0 ? 64u - __clzll(static_cast<unsigned long long>(m)) : 0u;
+    atomicAdd(&h[c], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 40 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void row_class_scan_kernel(uint32_t *hist) {  // one thread: offsets, largest class first
+  uint32_t run = 0;
+  for (int c = 39; c >= 0; --c) {
+    const uint32_t v = hist[c];
+    hist[c] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(256) row_class_scatter_kernel(const int64_t *row_ptr, int64_t n, uint32_t *offs,
+                                                                int32_t *order) {
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t m = row_ptr[r + 1] - row_ptr[r];
+    const uint32_t c = m > 0 ? 64u - __clzll(static_cast<unsigned long long>(m)) : 0u;
+    order[atomicAdd(&offs[c], 1u)] = static_cast<int32_t>(r);
+  }
+}
+
 }  // namespace
+
+int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t *hist40, cudaStream_t stream) {
+  if (n <= 0) return 0;
+  if (cudaMemsetAsync(hist40, 0, 40 * sizeof(uint32_t), stream) != cudaSuccess) return FLASH_ECUDA;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 8L * num_sms()) blocks = 8L * num_sms();
+  row_class_hist_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist40);
+  row_class_scan_kernel<<<1, 1, 0, stream>>>(hist40);
+  row_class_scatter_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist40, order);
+  count_launches(3);
+  return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
+}
 
 int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   DophParams a{};
@@ -386,6 +434,7 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.vec_out = !L.keys && (a.B % 4 == 0) && ((reinterpret_cast<uintptr_t>(L.out) & 15) == 0);
   a.err = L.err;
   a.row_counter = L.row_counter;
+  a.order = L.order;
   const double avg = L.n_rows > 0 ? static_cast<double>(L.nnz) / static_cast<double>(L.n_rows) : 1.0;
   uint32_t g = static_cast<uint32_t>(2048.0 / (avg + 16.0) + 1.0);
   a.rows_per_grab = g < 1 ? 1 : (g > 64 ? 64 : g);

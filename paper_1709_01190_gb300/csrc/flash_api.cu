@@ -69,10 +69,13 @@ struct PhaseTimer {
 };
 thread_local PhaseTimer g_timer;
 
-uint32_t env_u32(const char *name, uint32_t dflt) {
-  const char *v = getenv(name);
-  if (!v || !*v) return dflt;
-  return static_cast<uint32_t>(strtoul(v, nullptr, 10));
+// Launch knobs (flash_set_tuning); every call copies them once at its start.
+std::mutex g_tuning_mu;
+flash_tuning g_tuning = {0, 0, 0};
+
+flash_tuning current_tuning() {
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  return g_tuning;
 }
 
 // One stream-ordered allocation carved into 256-byte aligned parts.
@@ -128,8 +131,9 @@ int check_csr(const flash_csr *x) {
 }
 
 DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, bool keys, uint32_t *out, int64_t ld,
-                     unsigned long long *counter) {
+                     unsigned long long *counter, const flash_tuning &tu) {
   DophLaunch d{};
+  d.rows_per_grab = tu.doph_rows_per_grab;
   d.row_ptr = x->row_ptr;
   d.col = x->col;
   d.n_rows = x->n_rows;
@@ -147,6 +151,23 @@ DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, 
   return d;
 }
 
+// Optional longest-rows-first order of the rows for the DOPH kernel.
+struct RowOrder {
+  int32_t *order = nullptr;
+  uint32_t *hist = nullptr;
+  void plan(Arena &ar, const flash_tuning &tu, int64_t n) {
+    if (tu.doph_order == 1 && n > 0) {
+      ar.add(&order, n);
+      ar.add(&hist, 40);
+    }
+  }
+  int apply(DophLaunch &d, const flash_csr *x, cudaStream_t st) {
+    if (!order) return 0;
+    d.order = order;
+    return build_row_order(x->row_ptr, x->n_rows, order, hist, st);
+  }
+};
+
 // scratch of build: keys, sorted keys, sort ping-pong, histograms, heavy list, counters
 struct BuildScratch {
   uint32_t *keys = nullptr, *skeys = nullptr, *tkeys = nullptr, *hist = nullptr;
@@ -156,10 +177,14 @@ struct BuildScratch {
   unsigned long long *counters = nullptr;
   int64_t heavy_cap = 0;
   SortPlan plan{};
+  RowOrder ro;
+  flash_tuning tu{};
 };
 
 void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, bool rowmajor_keys = false) {
   const int64_t ln = static_cast<int64_t>(p->L) * n;
+  b.tu = current_tuning();
+  b.ro.plan(ar, b.tu, n);
   b.plan = make_sort_plan(p->range_bits, n, p->L);
   b.heavy_cap = reservoir_heavy_capacity(n, p->L, p->R, p->range_bits);
   ar.add(&b.keys, ln);
@@ -177,9 +202,10 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
               uint32_t *starts, cudaStream_t st) {
   const int64_t n = x->n_rows;
   g_timer.mark("hash", st);
-  DophLaunch dl = doph_args(p, s, x, true, b.keys, n, b.counters);
+  DophLaunch dl = doph_args(p, s, x, true, b.keys, n, b.counters, b.tu);
   dl.out_rowmajor = b.keys_rm;
-  int rc = launch_doph(dl, st);
+  int rc = b.ro.apply(dl, x, st);
+  if (!rc) rc = launch_doph(dl, st);
   if (rc) return rc;
   g_timer.mark("sort", st);
   SortLaunch sl{};
@@ -231,7 +257,7 @@ QueryLaunch query_args(const flash_params *p, const uint32_t *qkeys, bool rowmaj
   q.out_counts = out_counts;
   q.counters = counters;
   q.overflow = overflow;
-  q.warp_table = env_u32("FLASH_QUERY_WARP_TABLE", 0);
+  q.warp_table = current_tuning().query_warp_table;
   return q;
 }
 
@@ -255,13 +281,18 @@ int flash_hash(const flash_params *p, const flash_csr *x, uint32_t *hashes, void
   if (x->n_rows > 0 && !hashes) return FLASH_EINVAL;
   if (x->n_rows == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const flash_tuning tu = current_tuning();
   Arena ar;
   unsigned long long *counter = nullptr;
+  RowOrder ro;
   ar.add(&counter, 1);
+  ro.plan(ar, tu, x->n_rows);
   if (int rc = ar.alloc(st)) return rc;
   flash_params q = *p;
   q.range_bits = 1;
-  return launch_doph(doph_args(&q, derive_seeds(p->seed), x, false, hashes, 0, counter), st);
+  DophLaunch dl = doph_args(&q, derive_seeds(p->seed), x, false, hashes, 0, counter, tu);
+  if (int rc = ro.apply(dl, x, st)) return rc;
+  return launch_doph(dl, st);
 }
 
 int flash_keys(const flash_params *p, const flash_csr *x, uint32_t *keys, void *stream) {
@@ -272,11 +303,16 @@ int flash_keys(const flash_params *p, const flash_csr *x, uint32_t *keys, void *
   if (x->n_rows > 0 && !keys) return FLASH_EINVAL;
   if (x->n_rows == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const flash_tuning tu = current_tuning();
   Arena ar;
   unsigned long long *counter = nullptr;
+  RowOrder ro;
   ar.add(&counter, 1);
+  ro.plan(ar, tu, x->n_rows);
   if (int rc = ar.alloc(st)) return rc;
-  return launch_doph(doph_args(p, derive_seeds(p->seed), x, true, keys, x->n_rows, counter), st);
+  DophLaunch dl = doph_args(p, derive_seeds(p->seed), x, true, keys, x->n_rows, counter, tu);
+  if (int rc = ro.apply(dl, x, st)) return rc;
+  return launch_doph(dl, st);
 }
 
 int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, void *stream) {
@@ -334,16 +370,20 @@ int flash_query(const flash_index *ix, const flash_csr *q, int32_t k, const int3
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const flash_params *p = &ix->p;
   const int64_t nq = q->n_rows;
+  const flash_tuning tu = current_tuning();
   Arena ar;
   uint32_t *qkeys = nullptr;
   unsigned long long *counters = nullptr;
   int64_t *overflow = nullptr;
+  RowOrder ro;
   ar.add(&qkeys, static_cast<int64_t>(p->L) * nq);
   ar.add(&counters, 8);
   ar.add(&overflow, nq);
+  ro.plan(ar, tu, nq);
   if (int rc = ar.alloc(st)) return rc;
-  DophLaunch dl = doph_args(p, ix->s, q, true, nullptr, nq, counters + 3);
+  DophLaunch dl = doph_args(p, ix->s, q, true, nullptr, nq, counters + 3, tu);
   dl.out_rowmajor = qkeys;
+  if (int rc = ro.apply(dl, q, st)) return rc;
   if (int rc = launch_doph(dl, st)) return rc;
   return launch_query(query_args(p, qkeys, true, nq, nq, ix->ids, ix->starts, ix->n, k, exclude_ids, false, out_ids,
                                  out_counts, counters, overflow),
@@ -487,6 +527,26 @@ const char *flash_strerror(int status) {
     case FLASH_EDATA: return "invalid input data found on the device";
     default: return "unknown status";
   }
+}
+
+int flash_set_tuning(const flash_tuning *t) {
+  flash_tuning v = {0, 0, 0};
+  if (t) {
+    v = *t;
+    if (v.query_warp_table && (v.query_warp_table < 64 || v.query_warp_table > 8192 ||
+                               (v.query_warp_table & (v.query_warp_table - 1))))
+      return FLASH_EINVAL;
+    if (v.doph_rows_per_grab > 4096 || v.doph_order > 1) return FLASH_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  g_tuning = v;
+  return 0;
+}
+
+int flash_get_tuning(flash_tuning *t) {
+  if (!t) return FLASH_EINVAL;
+  *t = current_tuning();
+  return 0;
 }
 
 int flash_enable_phase_timing(int on) {

@@ -39,8 +39,12 @@ struct DophLaunch {
   unsigned long long *row_counter;  // 8 bytes of device scratch
   uint32_t rows_per_grab;           // 0 = automatic
   int64_t max_blocks;               // 0 = automatic
+  const int32_t *order;             // optional row processing order (null = 0..n-1)
 };
 int launch_doph(const DophLaunch &l, cudaStream_t stream);
+// order[0..n) = row ids, longest rows first (rows binned by log2 of their length);
+// hist40: 40 words of scratch
+int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t *hist40, cudaStream_t stream);
 
 // ---- K2: per-table stable radix sort of bucket addresses + bucket starts
 struct SortPlan {

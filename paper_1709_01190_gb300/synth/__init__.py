@@ -117,6 +117,12 @@ class CSR:
     def nnz(self) -> int:
         return int(self.row_ptr[-1])
 
+    def slice(self, r0: int, r1: int) -> "CSR":
+        """Rows [r0, r1) as a new CSR whose row_ptr starts at 0 (views of the arrays)."""
+        a, b = int(self.row_ptr[r0]), int(self.row_ptr[r1])
+        val = None if self.val is None else self.val[a:b]
+        return CSR(self.row_ptr[r0:r1 + 1] - a, self.col[a:b], val, self.dim)
+
     def rows(self, ids) -> "CSR":
         """Gather a subset of rows into a new CSR (host)."""
         ids = np.asarray(ids, dtype=np.int64)

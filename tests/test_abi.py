@@ -58,3 +58,19 @@ def test_product_path_fails_loudly_without_a_gpu():
     import paper_1709_01190_gb300 as fl
     with pytest.raises(Exception):
         fl.hash_rows(fl.FlashParams(2, 2, 2, 4, 1), None)
+
+
+def test_tuning_knobs_roundtrip_and_validation(libflash):
+    from paper_1709_01190_gb300 import FlashError, tuning
+    try:
+        t = tuning.Tuning(query_warp_table=256, doph_rows_per_grab=8, doph_order=1)
+        tuning.set_tuning(t)
+        assert tuning.get_tuning() == t
+        for bad in (tuning.Tuning(query_warp_table=100), tuning.Tuning(query_warp_table=32),
+                    tuning.Tuning(doph_order=2), tuning.Tuning(doph_rows_per_grab=5000)):
+            with pytest.raises(FlashError):
+                tuning.set_tuning(bad)
+        assert tuning.get_tuning() == t      # a rejected setting changes nothing
+    finally:
+        tuning.set_tuning(None)
+    assert tuning.get_tuning() == tuning.Tuning()
