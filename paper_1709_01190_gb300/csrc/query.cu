@@ -5,11 +5,21 @@
 //   gather : the reservoir of bucket key_t(q) in table t is the first
 //            min(m, R) ids of its segment in the grouped table;
 //   count  : each id's number of occurrences over the L reservoirs goes into
-//            a shared-memory open-addressing table; an entry packs
+//            a shared-memory open-addressing table (linear probing).
+//            Warp path (a few hundred candidates): an entry packs
 //            (id + 1) << 8 | (count - 1) (id < 2^24 - 1, count <= L <= 256),
 //            inserted with atomicCAS and incremented with atomicAdd; each new
-//            entry's slot is appended to a list, so the distinct candidates
-//            need no scan of the table afterwards;
+//            entry's slot is appended to a list.  Block path (thousands of
+//            candidates, nearly all distinct): returning shared atomics (CAS,
+//            OR) have a small fraction of the throughput of non-returning
+//            ones (red) on this part, so tags id + 1 are placed in
+//            barrier-separated rounds instead: a read step probes to the
+//            id's slot or to the first empty one, a write step stores the tag
+//            into that empty slot (blind; the last writer wins) and the next
+//            read step finds whether this id won.  Counts go to a parallel
+//            array of 16-bit counters through red; the few ids still unplaced
+//            after the last round use atomicCAS.  The table is then
+//            compacted in place into sort keys;
 //   select : the k largest sort keys (count - 1) << 24 | (2^24 - 1 - id),
 //            i.e. count descending then id ascending, found by a radix select
 //            over 8-bit digits (histogram, suffix sum, threshold), collected
@@ -19,13 +29,16 @@
 // unique top-k of the (count desc, id asc) order, identical to sorting.
 //
 // Two launch shapes share the code through a Group (warp or block):
-//   query_warp_kernel : one warp per query, software-pipelined over the
-//                       queries of the warp: the next query's bucket ranges
-//                       are loaded while the current one is counted, and its
-//                       first candidate ids while the current one is
-//                       selected; queries whose candidates do not fit the
-//                       warp's table are appended to an overflow list;
-//   query_block_kernel: one block per overflow query, a table sized for L*R.
+//   query_warp_kernel: one warp per query, software-pipelined over the
+//                      queries of the warp: the next query's bucket ranges
+//                      are loaded while the current one is counted, and its
+//                      first candidate ids while the current one is
+//                      selected; queries whose candidates do not fit the
+//                      warp's table are appended to an overflow list;
+//   query_big_kernel : one block per overflow query (all queries when k is
+//                      too large for the warp path), in two tiers: a 64 KB
+//                      table first (several blocks per SM), then a table
+//                      sized for L*R for the few queries that do not fit it.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -37,7 +50,8 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kQWarps = 8;  // warps per block, warp kernel
-constexpr int kQBlockThreads = 256;
+constexpr int kBigThreads = 512;
+constexpr uint32_t kBigTable = 16384;  // slots of the first big tier's table (64 KB)
 constexpr int kBatch = 8;   // candidate ids a thread loads before counting them
 
 struct QArgs {
@@ -77,19 +91,21 @@ struct BlockGroup {
 };
 
 // Shared layout of one group:
-//   [tab S][lst S/2][pre 2x(L+1)][sb 2xL][hist 256][sel kp][misc 40]
+//   [tab S][aux S/2][pre 2x(L+1)][sb 2xL][hist 256][sel kp][misc 40]
+// aux is the list of new entries' slots (warp path) or the 16-bit counts
+// (block path).
 // pre/sb are double-buffered: the pipelined warp kernel builds the next
 // query's bucket ranges while the current query still uses its own.
 struct Region {
-  uint32_t *tab, *lst, *pre[2], *sb[2], *hist, *sel, *misc;
+  uint32_t *tab, *aux, *pre[2], *sb[2], *hist, *sel, *misc;
 };
 
 __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
   Region r;
   const uint32_t lp = (a.L + 1 + 3) & ~3u;
   r.tab = base;
-  r.lst = r.tab + a.table_words;
-  r.pre[0] = r.lst + a.table_words / 2;
+  r.aux = r.tab + a.table_words;
+  r.pre[0] = r.aux + a.table_words / 2;
   r.pre[1] = r.pre[0] + lp;
   r.sb[0] = r.pre[1] + lp;
   r.sb[1] = r.sb[0] + lp;
@@ -101,11 +117,17 @@ __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
 
 uint32_t region_words(const QArgs &a) {
   const uint32_t lp = (a.L + 1 + 3) & ~3u;
-  return a.table_words + a.table_words / 2 + 4 * lp + 256 + a.kp + 40;
+  const uint32_t w = a.table_words + a.table_words / 2 + 4 * lp + 256 + a.kp + 40;
+  return (w + 3) & ~3u;  // every group's table starts on 16 bytes (uint4 reads)
 }
 
-__device__ __forceinline__ uint32_t sort_key(uint32_t e) {
-  // e = (id + 1) << 8 | (count - 1)  ->  (count - 1) << 24 | (2^24 - 1 - id)
+// Tag id + 1 and count c >= 1  ->  (c - 1) << 24 | (2^24 - 1 - id).
+__device__ __forceinline__ uint32_t sort_key(uint32_t tag, uint32_t c) {
+  return ((c - 1u) << 24) | (0xFFFFFFu - (tag - 1u));
+}
+
+// Packed entry (id + 1) << 8 | (count - 1)  ->  the same sort key.
+__device__ __forceinline__ uint32_t sort_key_packed(uint32_t e) {
   return ((e & 0xFFu) << 24) | (0xFFFFFFu - ((e >> 8) - 1u));
 }
 
@@ -210,18 +232,31 @@ __device__ void write_empty(const G &g, const QArgs &a, int64_t q) {
   }
 }
 
+// Count table of a query with M candidates, warp path: a power of two >= 2 M
+// (load <= 1/2).
 __device__ __forceinline__ uint32_t table_size(uint32_t M) {
   uint32_t S = 64;
   while (S < 2 * M) S <<= 1;
   return S;
 }
 
-// COUNTFREQUENCY into tab (S >= 2M slots).  The first batch of ids is given
-// (loaded ahead by the caller); later batches are loaded here with a cursor
-// of their own.  The slot of every new entry goes to lst; misc[4] = E.
-template <class G>
-__device__ void count_phase(const G &g, const QArgs &a, const Region &r, const uint32_t *pre, const uint32_t *sb,
-                            int64_t q, uint32_t M, const int32_t (&first)[kBatch]) {
+// Count table of the block path: a power of two > 1.5 M (load < 2/3).
+__host__ __device__ __forceinline__ uint32_t big_table_size(uint32_t M) {
+  uint32_t S = 64;
+  while (S < M + M / 2 + 1) S <<= 1;
+  return S;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(int32_t id, uint32_t lg) {
+  return (static_cast<uint32_t>(id) * 0x9E3779B1u) >> (32 - lg);
+}
+
+// COUNTFREQUENCY of the warp path into packed entries (S >= 2M slots).  The
+// first batch of ids is given (loaded ahead by the caller); later batches are
+// loaded here with a cursor of their own.  The slot of every new entry goes to
+// the list aux; misc[4] = E.
+__device__ void count_phase_warp(const WarpGroup &g, const QArgs &a, const Region &r, const uint32_t *pre,
+                                 const uint32_t *sb, int64_t q, uint32_t M, const int32_t (&first)[kBatch]) {
   const uint32_t S = table_size(M);
   const uint32_t lg = ilog2_pow2(S);
   for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
@@ -238,13 +273,13 @@ __device__ void count_phase(const G &g, const QArgs &a, const Region &r, const u
       const int32_t id = idv[j];
       if (id < 0 || id == excl) continue;
       const uint32_t tag = (static_cast<uint32_t>(id) + 1u) << 8;
-      uint32_t h = (static_cast<uint32_t>(id) * 0x9E3779B1u) >> (32 - lg);
+      uint32_t h = slot_hash(id, lg);
       for (;;) {
         uint32_t cur = r.tab[h];
         if (cur == 0) {
           cur = atomicCAS(&r.tab[h], 0u, tag);
           if (cur == 0) {
-            r.lst[atomicAdd(&r.misc[4], 1u)] = h;
+            r.aux[atomicAdd(&r.misc[4], 1u)] = h;
             break;
           }
         }
@@ -255,6 +290,114 @@ __device__ void count_phase(const G &g, const QArgs &a, const Region &r, const u
         h = (h + 1) & (S - 1);
       }
     }
+    base += kBatch * g.size();
+    if (base >= M) break;
+    load_ids(g, a, pre, sb, M, base, cursor, idv);
+  }
+  g.sync();
+}
+
+// Sort keys of the distinct candidates listed in aux (warp path); returns E.
+__device__ __forceinline__ uint32_t keys_from_list(const WarpGroup &g, const Region &r) {
+  const uint32_t E = r.misc[4];
+  for (uint32_t i = g.rank(); i < E; i += g.size()) r.aux[i] = sort_key_packed(r.tab[r.aux[i]]);
+  g.sync();
+  return E;
+}
+
+// 16-bit counts, two per word: a non-returning add (counts <= L <= 256).
+__device__ __forceinline__ void count_add(uint32_t *cnt, uint32_t h) {
+  atomicAdd(&cnt[h >> 1], 1u << ((h & 1u) << 4));
+}
+
+// COUNTFREQUENCY of one batch of ids (idv[j] < 0: none; the excluded id is
+// skipped), block path; every thread of the block calls it.  Rounds of
+//   read  : probe from h to this id's tag (placed: count it) or to the first
+//           empty slot (to be written); only reads happen in this step;
+//   write : store the tag into that slot; only writes happen in this step;
+// separated by barriers, so every read sees a stable table and a lost write
+// race shows up in the next read step.  Ids still unplaced after kRounds
+// rounds are inserted with atomicCAS once the block's writes are done.
+__device__ __forceinline__ void count_batch(const BlockGroup &g, const Region &r, uint32_t S, uint32_t lg,
+                                            const int32_t (&idv)[kBatch], int32_t excl) {
+  constexpr int kRounds = 3;
+  uint32_t h[kBatch];
+  uint32_t pend = 0;
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    h[j] = 0;
+    if (idv[j] >= 0 && idv[j] != excl) {
+      pend |= 1u << j;
+      h[j] = slot_hash(idv[j], lg);
+    }
+  }
+  g.sync();  // the previous batch's writes are visible
+  bool done = false;
+  for (int round = 0; round < kRounds; ++round) {
+    uint32_t want = 0;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if ((pend >> j) & 1u) {
+        const uint32_t tag = static_cast<uint32_t>(idv[j]) + 1u;
+        for (;;) {
+          const uint32_t w = r.tab[h[j]];
+          if (w == tag) {
+            count_add(r.aux, h[j]);
+            pend &= ~(1u << j);
+            break;
+          }
+          if (w == 0) {
+            want |= 1u << j;
+            break;
+          }
+          h[j] = (h[j] + 1) & (S - 1);
+        }
+      }
+    }
+    if (!__syncthreads_or(want != 0)) {
+      done = true;
+      break;
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+      if ((want >> j) & 1u) r.tab[h[j]] = static_cast<uint32_t>(idv[j]) + 1u;
+    g.sync();
+  }
+  if (done) return;
+  // the last round's writes are visible: settle them, then CAS the rest
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    if ((pend >> j) & 1u) {
+      const uint32_t tag = static_cast<uint32_t>(idv[j]) + 1u;
+      for (;;) {
+        uint32_t w = r.tab[h[j]];
+        if (w == 0) w = atomicCAS(&r.tab[h[j]], 0u, tag);
+        if (w == 0 || w == tag) {
+          count_add(r.aux, h[j]);
+          break;
+        }
+        h[j] = (h[j] + 1) & (S - 1);
+      }
+    }
+  }
+}
+
+// COUNTFREQUENCY of the block path into a table of S slots (tags in tab,
+// counts in aux).  The first batch of ids is given (loaded ahead by the
+// caller); later batches are loaded here with a cursor of their own.
+__device__ void count_phase_block(const BlockGroup &g, const QArgs &a, const Region &r, const uint32_t *pre,
+                                  const uint32_t *sb, int64_t q, uint32_t M, const int32_t (&first)[kBatch],
+                                  uint32_t S) {
+  const uint32_t lg = ilog2_pow2(S);
+  for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
+  for (uint32_t i = g.rank(); i < S / 2; i += g.size()) r.aux[i] = 0;
+  const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
+  uint32_t cursor = 0;
+  int32_t idv[kBatch];
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) idv[j] = first[j];
+  for (uint32_t base = 0;;) {
+    count_batch(g, r, S, lg, idv, excl);
     base += kBatch * g.size();
     if (base >= M) break;
     load_ids(g, a, pre, sb, M, base, cursor, idv);
@@ -326,16 +469,48 @@ __device__ __forceinline__ void warp_sort_and_write(const QArgs &a, const uint32
   }
 }
 
-// Sort keys of the E distinct candidates (in lst), radix select of the k-th
-// largest, collection and sorted output (SORTBYVALUE, then the first k).
-template <class G>
-__device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_t q) {
-  uint32_t *misc = r.misc;  // [0]=prefix [1]=pmask [2]=need [3]=done [4]=E [5]=nsel
-  const uint32_t E = misc[4];
-  uint32_t *keys = r.lst;
-  for (uint32_t i = g.rank(); i < E; i += g.size()) keys[i] = sort_key(r.tab[keys[i]]);
-  g.sync();
+// nsel <= 256 winners sorted by one warp.
+__device__ __forceinline__ void warp_sort_winners(const QArgs &a, const uint32_t *sel, uint32_t nsel, int64_t q) {
+  if (nsel <= 32) warp_sort_and_write<1>(a, sel, nsel, q);
+  else if (nsel <= 64) warp_sort_and_write<2>(a, sel, nsel, q);
+  else if (nsel <= 128) warp_sort_and_write<4>(a, sel, nsel, q);
+  else warp_sort_and_write<8>(a, sel, nsel, q);
+}
 
+// nsel winners sorted by the block (bitonic network over kp slots in shared memory).
+__device__ void block_sort_winners(const QArgs &a, uint32_t *sel, uint32_t nsel, int64_t q) {
+  for (uint32_t i = nsel + threadIdx.x; i < a.kp; i += blockDim.x) sel[i] = 0;
+  __syncthreads();
+  for (uint32_t size = 2; size <= a.kp; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < a.kp / 2; i += blockDim.x) {
+        const uint32_t lo = (i / stride) * stride * 2 + (i % stride), hi = lo + stride;
+        const bool desc = (lo & size) == 0;
+        const uint32_t x = sel[lo], y = sel[hi];
+        if ((x < y) == desc) {
+          sel[lo] = y;
+          sel[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
+    const uint32_t key = sel[j];
+    __stcs(a.out_ids + q * a.k + j, key ? static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)) : -1);
+    __stcs(a.out_counts + q * a.k + j, key ? static_cast<int32_t>((key >> 24) + 1u) : 0);
+  }
+}
+
+// Radix select of the k-th largest of keys[0..E) (SORTBYVALUE, then the first
+// k), collection and sorted output.  Histogram updates are aggregated per warp
+// (__match_any_sync) because the digits are very skewed (most counts are 1).
+template <class G>
+__device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_t q, const uint32_t *keys,
+                             uint32_t E) {
+  uint32_t *misc = r.misc;  // [0]=prefix [1]=pmask [2]=need [3]=done [5]=nsel
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   uint32_t thr = 1;  // E <= k: every key is selected
   if (E > static_cast<uint32_t>(a.k)) {
     if (g.rank() == 0) {
@@ -349,13 +524,15 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
       for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
       g.sync();
       const uint32_t prefix = misc[0], pmask = misc[1];
-      for (uint32_t i = g.rank(); i < E; i += g.size()) {
-        const uint32_t key = keys[i];
-        if ((key & pmask) == prefix) atomicAdd(&r.hist[(key >> shift) & 0xFFu], 1u);
+      for (uint32_t base = 0; base < E; base += g.size()) {
+        const uint32_t i = base + g.rank();
+        const uint32_t key = i < E ? keys[i] : 0u;
+        const uint32_t d = (i < E && (key & pmask) == prefix) ? ((key >> shift) & 0xFFu) : 0x100u;
+        const uint32_t peers = __match_any_sync(kFull, d);
+        if (d != 0x100u && (peers & lt) == 0) atomicAdd(&r.hist[d], __popc(peers));
       }
       g.sync();
       if (g.leader_warp()) {
-        const int lane = threadIdx.x & 31;
         uint32_t s = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i) s += r.hist[lane * 8 + i];
@@ -405,35 +582,58 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
   g.sync();
   const uint32_t nsel = misc[5] < a.kp ? misc[5] : a.kp;
   if constexpr (G::kIsWarp) {
-    if (nsel <= 32) warp_sort_and_write<1>(a, r.sel, nsel, q);
-    else if (nsel <= 64) warp_sort_and_write<2>(a, r.sel, nsel, q);
-    else if (nsel <= 128) warp_sort_and_write<4>(a, r.sel, nsel, q);
-    else warp_sort_and_write<8>(a, r.sel, nsel, q);
-    g.sync();
+    warp_sort_winners(a, r.sel, nsel, q);
+  } else if (a.kp <= 256) {  // one warp sorts the winners in registers
+    if (threadIdx.x < 32) warp_sort_winners(a, r.sel, nsel, q);
   } else {
-    for (uint32_t i = nsel + g.rank(); i < a.kp; i += g.size()) r.sel[i] = 0;
-    g.sync();
-    for (uint32_t size = 2; size <= a.kp; size <<= 1) {
-      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-        for (uint32_t i = g.rank(); i < a.kp / 2; i += g.size()) {
-          const uint32_t lo = (i / stride) * stride * 2 + (i % stride), hi = lo + stride;
-          const bool desc = (lo & size) == 0;
-          const uint32_t x = r.sel[lo], y = r.sel[hi];
-          if ((x < y) == desc) {
-            r.sel[lo] = y;
-            r.sel[hi] = x;
-          }
-        }
-        g.sync();
-      }
-    }
-    for (int j = g.rank(); j < a.k; j += g.size()) {
-      const uint32_t key = r.sel[j];
-      __stcs(a.out_ids + q * a.k + j, key ? static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)) : -1);
-      __stcs(a.out_counts + q * a.k + j, key ? static_cast<int32_t>((key >> 24) + 1u) : 0);
-    }
-    g.sync();
+    block_sort_winners(a, r.sel, nsel, q);
   }
+  g.sync();
+}
+
+// Ordered in-place compaction of the non-empty entries of tab[0..S) (tags;
+// counts in cnt) into their sort keys tab[0..E), four slots per thread and
+// round (block path).  Writes never pass the read frontier: an entry's rank
+// among the non-empty entries is at most its index, and a round's reads all
+// finish before its writes.  `scratch` holds a word per warp.
+__device__ uint32_t compact_keys(const BlockGroup &g, uint32_t *tab, const uint32_t *cnt, uint32_t S,
+                                 uint32_t *scratch) {
+  const int lane = threadIdx.x & 31;
+  uint32_t out = 0;
+  for (uint32_t base = 0; base < S; base += 4 * g.size()) {
+    const uint32_t i = base + 4 * g.rank();
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    uint2 c2 = make_uint2(0u, 0u);
+    if (i < S) {
+      e = *reinterpret_cast<const uint4 *>(tab + i);
+      c2 = *reinterpret_cast<const uint2 *>(cnt + i / 2);
+    }
+    const uint32_t c = (e.x != 0) + (e.y != 0) + (e.z != 0) + (e.w != 0);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += x;
+    }
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 31) scratch[warp] = inc;
+    g.sync();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      const uint32_t cw = scratch[w];
+      if (w < warp) before += cw;
+      total += cw;
+    }
+    g.sync();
+    uint32_t pos = out + before + inc - c;
+    if (e.x) tab[pos++] = sort_key(e.x, c2.x & 0xFFFFu);
+    if (e.y) tab[pos++] = sort_key(e.y, c2.x >> 16);
+    if (e.z) tab[pos++] = sort_key(e.z, c2.y & 0xFFFFu);
+    if (e.w) tab[pos] = sort_key(e.w, c2.y >> 16);
+    out += total;
+  }
+  g.sync();
+  return out;
 }
 
 __device__ __forceinline__ unsigned long long claim_query(const QArgs &a) {
@@ -464,14 +664,14 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
   uint32_t M = build_ranges<TPL>(g, a, pre_c, sb_c, s, e);
   int32_t ids[kBatch];
   uint32_t cur0 = 0;
-  load_ids(g, a, pre_c, sb_c, 2 * M <= a.table_words ? M : 0, 0, cur0, ids);
+  load_ids(g, a, pre_c, sb_c, table_size(M) <= a.table_words ? M : 0, 0, cur0, ids);
 
   while (q < nq) {
     // the next query's bucket ranges are in flight while this one is counted
     uint32_t sn[TPL], en[TPL];
     load_ranges<TPL>(g, a, keys_n, sn, en);
-    const bool fits = 2 * M <= a.table_words;
-    if (M > 0 && fits) count_phase(g, a, r, pre_c, sb_c, static_cast<int64_t>(q), M, ids);
+    const bool fits = table_size(M) <= a.table_words;
+    if (M > 0 && fits) count_phase_warp(g, a, r, pre_c, sb_c, static_cast<int64_t>(q), M, ids);
 
     // stage the next query: its ranges into the other buffer, its first ids in flight
     const unsigned long long qn2 = claim_query(a);
@@ -479,14 +679,15 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
     load_query_keys<TPL>(g, a, static_cast<int64_t>(qn2), keys_n2);
     const uint32_t Mn = build_ranges<TPL>(g, a, pre_n, sb_n, sn, en);
     uint32_t curn = 0;
-    load_ids(g, a, pre_n, sb_n, 2 * Mn <= a.table_words ? Mn : 0, 0, curn, ids);
+    load_ids(g, a, pre_n, sb_n, table_size(Mn) <= a.table_words ? Mn : 0, 0, curn, ids);
 
     if (M == 0) {
       write_empty(g, a, static_cast<int64_t>(q));
     } else if (!fits) {
       if (lane == 0) a.overflow[atomicAdd(a.over_count, 1ULL)] = static_cast<int64_t>(q);
     } else {
-      select_phase(g, a, r, static_cast<int64_t>(q));
+      const uint32_t E = keys_from_list(g, r);
+      select_phase(g, a, r, static_cast<int64_t>(q), r.aux, E);
     }
     __syncwarp();
 
@@ -504,28 +705,53 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kQBlockThreads) query_block_kernel(QArgs a, int all_queries) {
+// One block per query of the overflow list (all queries with all_queries).
+// Tier 1 takes the queries whose candidates fit a.table_words slots at load
+// below 2/3 and marks the others overflow[h] = -(q + 1) (with all_queries it
+// writes every entry: q or the mark); tier 2 takes exactly the marked ones.
+__global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int all_queries, int tier) {
   extern __shared__ uint32_t smem[];
   const BlockGroup g;
   const Region r = carve(smem, a);
   const int64_t count = all_queries ? a.nq : static_cast<int64_t>(*a.over_count);
   for (int64_t h = blockIdx.x; h < count; h += gridDim.x) {
-    const int64_t q = all_queries ? h : a.overflow[h];
+    int64_t q;
+    if (tier == 1) {
+      q = all_queries ? h : a.overflow[h];
+    } else {
+      const int64_t v = a.overflow[h];
+      if (v >= 0) continue;
+      q = -v - 1;
+    }
     uint32_t keys[1], s[1], e[1];
     load_query_keys<1>(g, a, q, keys);  // blockDim >= L: one table per thread
     load_ranges<1>(g, a, keys, s, e);
     const uint32_t M = build_ranges<1>(g, a, r.pre[0], r.sb[0], s, e);
-    if (M == 0) {
+    const uint32_t S = big_table_size(M);
+    const bool defer = tier == 1 && S > a.table_words;
+    if (tier == 1 && threadIdx.x == 0 && (defer || all_queries)) a.overflow[h] = defer ? -q - 1 : q;
+    if (defer) {
+      // left to tier 2
+    } else if (M == 0) {
       write_empty(g, a, q);
-      g.sync();
     } else {
       int32_t ids[kBatch];
       uint32_t cur = 0;
       load_ids(g, a, r.pre[0], r.sb[0], M, 0, cur, ids);
-      count_phase(g, a, r, r.pre[0], r.sb[0], q, M, ids);
-      select_phase(g, a, r, q);
+      count_phase_block(g, a, r, r.pre[0], r.sb[0], q, M, ids, S);
+      const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
+      select_phase(g, a, r, q, r.tab, E);
     }
+    g.sync();
   }
+}
+
+size_t max_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return static_cast<size_t>(v);
 }
 
 uint32_t next_pow2(uint32_t x) {
@@ -579,14 +805,18 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
   a.overflow = l.overflow;
   if (cudaMemsetAsync(l.counters, 0, 2 * sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
 
-  const uint32_t full_table = next_pow2(2 * l.L * l.R) < 64 ? 64 : next_pow2(2 * l.L * l.R);
   const bool warp_ok = l.k <= 256;
   int all = 1;
   if (warp_ok) {
+    const uint32_t full_table = next_pow2(2 * l.L * l.R) < 64 ? 64 : next_pow2(2 * l.L * l.R);
     uint32_t tw = l.warp_table ? l.warp_table : 512u;
     if (tw > full_table) tw = full_table;
     a.table_words = tw;
     a.region_words = region_words(a);
+    while (a.table_words > 64 && static_cast<size_t>(kQWarps) * a.region_words * sizeof(uint32_t) > max_smem_optin()) {
+      a.table_words >>= 1;  // a tuned table too large for this device's shared memory
+      a.region_words = region_words(a);
+    }
     const uint32_t tpl = (l.L + 31) / 32;
     int rc;
     if (tpl <= 1) rc = launch_warp<1>(a, l.nq, stream);
@@ -596,20 +826,27 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
     if (rc) return rc;
     all = 0;
   }
-  a.table_words = full_table;
-  a.region_words = region_words(a);
-  const size_t smem_b = static_cast<size_t>(a.region_words) * sizeof(uint32_t);
-  if (cudaFuncSetAttribute(query_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem_b)) != cudaSuccess)
-    return FLASH_ECUDA;
-  int per_sm_b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, query_block_kernel, kQBlockThreads, smem_b) !=
-      cudaSuccess)
-    return FLASH_ECUDA;
-  if (per_sm_b < 1) return FLASH_EINVAL;
-  const int64_t blocks_b = static_cast<int64_t>(per_sm_b) * num_sms();
-  query_block_kernel<<<static_cast<unsigned>(blocks_b), kQBlockThreads, smem_b, stream>>>(a, all);
-  count_launches(1);
+  // block path: tier 1 with a 64 KB table (or one sized for L*R when smaller),
+  // tier 2 with a table sized for L*R when some query may not fit tier 1
+  const uint32_t need = big_table_size(l.L * l.R);
+  const uint32_t tw1 = need < kBigTable ? need : kBigTable;
+  for (int tier = 1; tier <= (need > tw1 ? 2 : 1); ++tier) {
+    a.table_words = tier == 1 ? tw1 : need;
+    a.region_words = region_words(a);
+    const size_t smem_b = static_cast<size_t>(a.region_words) * sizeof(uint32_t);
+    if (cudaFuncSetAttribute(query_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem_b)) != cudaSuccess)
+      return FLASH_ECUDA;
+    int per_sm_b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, query_big_kernel, kBigThreads, smem_b) !=
+        cudaSuccess)
+      return FLASH_ECUDA;
+    if (per_sm_b < 1) return FLASH_EINVAL;
+    int64_t blocks_b = static_cast<int64_t>(per_sm_b) * num_sms();
+    if (all && blocks_b > l.nq) blocks_b = l.nq;
+    query_big_kernel<<<static_cast<unsigned>(blocks_b), kBigThreads, smem_b, stream>>>(a, all, tier);
+    count_launches(1);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }
 

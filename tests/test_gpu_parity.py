@@ -173,25 +173,36 @@ QUERY_CASES = [
     ("kdd12_like", 30_000, dict(range_bits=14), 32, 0),
     ("tiny_plain", 3_000, dict(range_bits=5, R=8), 1, 0),
     ("tiny_plain", 3_000, dict(range_bits=5, R=8), 300, 0),      # k > 256: block path only
+    # block path, second tier: most reservoirs full (M near L*R = 16384 > the 64 KB table's 10922)
+    ("url_like_batched", 20_000, dict(range_bits=6, K=1), 64, 0),
+    # both block tiers mixed (M spread around 10922), k = 200 sorted by one warp
+    ("url_like_batched", 20_000, dict(range_bits=8, K=1), 200, 64),
+    # k > 256 with second-tier queries: every query on the block path, block bitonic sort
+    ("url_like_batched", 20_000, dict(range_bits=7, K=1), 300, 0),
 ]
 
 
 @pytest.mark.parametrize("name,n,over,k,wt", QUERY_CASES)
-def test_query_sampled_rows_with_exclusion(name, n, over, k, wt, monkeypatch):
+def test_query_sampled_rows_with_exclusion(name, n, over, k, wt):
+    from paper_1709_01190_gb300 import tuning
     w = synth.WORKLOADS[name].scaled(n)
     c = synth.generate(w.data)
     p = _params_override(w, over)
-    if wt:
-        monkeypatch.setenv("FLASH_QUERY_WARP_TABLE", str(wt))
     dev = fl.DeviceCSR.from_host(c)
     ix = fl.flash_build(p, dev)
     qids = synth.sample_rows(c.n_rows, min(400, c.n_rows), seed=5)
     sub = c.rows(qids)
     excl = torch.from_numpy(qids.astype(np.int32)).cuda()
-    ids, cnt = fl.query(ix, fl.DeviceCSR.from_host(sub), k, excl)
+    if wt:  # a warp table this small sends most queries to the block path
+        tuning.set_tuning(tuning.Tuning(query_warp_table=wt))
+    try:
+        ids, cnt = fl.query(ix, fl.DeviceCSR.from_host(sub), k, excl)
+    finally:
+        tuning.set_tuning(None)
     et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
     ei, en = oracle.query(et, ec, p.K, p.L, p.R, p.range_bits, p.seed, sub.row_ptr, sub.col, k,
                           exclude=qids.astype(np.int32))
+    assert fl.flash_device_error() == 0
     assert np.array_equal(ids.cpu().numpy(), ei)
     assert np.array_equal(cnt.cpu().numpy(), en)
 
