@@ -51,6 +51,8 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kQWarps = 8;  // warps per block, warp kernel
 constexpr int kBigThreads = 512;
+constexpr int kBigWarps = kBigThreads / 32;
+constexpr int kMaxTabPerWarp = 256 / kBigWarps;  // L <= 256
 constexpr uint32_t kBigTable = 16384;  // slots of the first big tier's table (64 KB)
 constexpr int kBatch = 8;   // candidate ids a thread loads before counting them
 
@@ -98,6 +100,10 @@ struct BlockGroup {
 // query's bucket ranges while the current query still uses its own.
 struct Region {
   uint32_t *tab, *aux, *pre[2], *sb[2], *hist, *sel, *misc;
+  // block path only: per-table reservoir sizes and segment starts, and each
+  // warp's candidate stream (table starts in the stream, element offsets)
+  uint32_t *mt, *sbk, *wpre;
+  long long *off;
 };
 
 __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
@@ -113,6 +119,29 @@ __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
   r.sel = r.hist + 256;
   r.misc = r.sel + a.kp;
   return r;
+}
+
+// Block path: [tab S][aux S/2][mt 256][sbk 256][wpre 16x17 (+pad)][off 16x16 x2][hist 256][sel kp][misc 40]
+constexpr uint32_t kWpreWords = (kBigWarps * (kMaxTabPerWarp + 1) + 3) & ~3u;
+
+__device__ __forceinline__ Region carve_big(uint32_t *base, const QArgs &a) {
+  Region r{};
+  r.tab = base;
+  r.aux = r.tab + a.table_words;
+  r.mt = r.aux + a.table_words / 2;
+  r.sbk = r.mt + 256;
+  r.wpre = r.sbk + 256;
+  r.off = reinterpret_cast<long long *>(r.wpre + kWpreWords);
+  r.hist = reinterpret_cast<uint32_t *>(r.off + kBigWarps * kMaxTabPerWarp);
+  r.sel = r.hist + 256;
+  r.misc = r.sel + a.kp;
+  return r;
+}
+
+uint32_t big_region_words(const QArgs &a) {
+  const uint32_t w = a.table_words + a.table_words / 2 + 512 + kWpreWords + 2 * kBigWarps * kMaxTabPerWarp + 256 +
+                     a.kp + 40;
+  return (w + 3) & ~3u;
 }
 
 uint32_t region_words(const QArgs &a) {
@@ -305,6 +334,79 @@ __device__ __forceinline__ uint32_t keys_from_list(const WarpGroup &g, const Reg
   return E;
 }
 
+// Block path: the L bucket ranges of query q, split into one candidate stream
+// per warp (warp w takes tables w, w + 16, ...).  wpre[w][i] is the start of
+// the warp's i-th table in its stream (wpre[w][ntab] = the stream's length) and
+// off[w][i] the element offset such that stream position x of that table is
+// ids[off + x].  Returns M, the number of candidates; misc[9] = the longest
+// stream.
+__device__ uint32_t build_streams(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    r.misc[8] = 0;
+    r.misc[9] = 0;
+  }
+  const uint32_t t = threadIdx.x;  // blockDim >= L: one table per thread
+  if (t < a.L) {
+    const uint32_t key = (q >= 0 && q < a.nq) ? query_key(a, q, t) : a.T;
+    uint32_t s = 0, e = 0;
+    if (key < a.T) {
+      const uint64_t keep = l2_policy_keep();
+      const uint32_t *st = a.starts + static_cast<int64_t>(t) * (static_cast<int64_t>(a.T) + 1);
+      s = ld_l2(st + key, keep);
+      e = ld_l2(st + key + 1, keep);
+    }
+    const uint32_t m = e - s;
+    r.mt[t] = m < a.R ? m : a.R;
+    r.sbk[t] = s;
+  }
+  g.sync();
+  const uint32_t w = static_cast<uint32_t>(warp);
+  const uint32_t ntab = a.L > w ? (a.L - w + kBigWarps - 1) / kBigWarps : 0;
+  const uint32_t tt = w + kBigWarps * static_cast<uint32_t>(lane);
+  const uint32_t v = static_cast<uint32_t>(lane) < ntab ? r.mt[tt] : 0u;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += x;
+  }
+  const uint32_t total = __shfl_sync(kFull, inc, 31);
+  uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
+  long long *of = r.off + warp * kMaxTabPerWarp;
+  if (static_cast<uint32_t>(lane) < ntab) {
+    wp[lane] = inc - v;
+    of[lane] = static_cast<long long>(tt) * a.n + r.sbk[tt] - (inc - v);
+  }
+  if (lane == 0) {
+    wp[ntab] = total;
+    if (total) {
+      atomicAdd(&r.misc[8], total);
+      atomicMax(&r.misc[9], total);
+    }
+  }
+  g.sync();
+  return r.misc[8];
+}
+
+// Candidate ids at stream positions base + 32 j + lane (j < kBatch) of this
+// warp's stream (tables starts wp, offsets of, length len); -1 past its end.
+// A lane's position only grows, so `cur` walks the warp's tables forward.
+__device__ __forceinline__ void load_stream_ids(const QArgs &a, const uint32_t *wp, const long long *of, uint32_t len,
+                                                uint32_t base, uint32_t &cur, int32_t (&idv)[kBatch]) {
+  const uint64_t keep = l2_policy_keep();
+  const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    const uint32_t x = base + 32 * j + lane;
+    idv[j] = -1;
+    if (x < len) {
+      while (wp[cur + 1] <= x) ++cur;
+      idv[j] = ld_l2(a.ids + of[cur] + x, keep);
+    }
+  }
+}
+
 // 16-bit counts, two per word: a non-returning add (counts <= L <= 256).
 __device__ __forceinline__ void count_add(uint32_t *cnt, uint32_t h) {
   atomicAdd(&cnt[h >> 1], 1u << ((h & 1u) << 4));
@@ -383,24 +485,27 @@ __device__ __forceinline__ void count_batch(const BlockGroup &g, const Region &r
 }
 
 // COUNTFREQUENCY of the block path into a table of S slots (tags in tab,
-// counts in aux).  The first batch of ids is given (loaded ahead by the
-// caller); later batches are loaded here with a cursor of their own.
-__device__ void count_phase_block(const BlockGroup &g, const QArgs &a, const Region &r, const uint32_t *pre,
-                                  const uint32_t *sb, int64_t q, uint32_t M, const int32_t (&first)[kBatch],
-                                  uint32_t S) {
+// counts in aux), over nbatch batches of each warp's stream.  The first batch
+// of ids is given (loaded ahead by the caller); later batches are loaded here.
+__device__ void count_phase_block(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q, uint32_t nbatch,
+                                  const int32_t (&first)[kBatch], uint32_t &cur, uint32_t S) {
   const uint32_t lg = ilog2_pow2(S);
-  for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
-  for (uint32_t i = g.rank(); i < S / 2; i += g.size()) r.aux[i] = 0;
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t i = 4 * g.rank(); i < S; i += 4 * g.size()) *reinterpret_cast<uint4 *>(r.tab + i) = z;
+  for (uint32_t i = 4 * g.rank(); i < S / 2; i += 4 * g.size()) *reinterpret_cast<uint4 *>(r.aux + i) = z;
   const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
-  uint32_t cursor = 0;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
+  const long long *of = r.off + warp * kMaxTabPerWarp;
+  const uint32_t ntab = a.L > static_cast<uint32_t>(warp) ? (a.L - warp + kBigWarps - 1) / kBigWarps : 0;
+  const uint32_t len = wp[ntab];
   int32_t idv[kBatch];
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) idv[j] = first[j];
-  for (uint32_t base = 0;;) {
+  for (uint32_t b = 0;;) {
     count_batch(g, r, S, lg, idv, excl);
-    base += kBatch * g.size();
-    if (base >= M) break;
-    load_ids(g, a, pre, sb, M, base, cursor, idv);
+    if (++b >= nbatch) break;
+    load_stream_ids(a, wp, of, len, b * 32 * kBatch, cur, idv);
   }
   g.sync();
 }
@@ -636,6 +741,126 @@ __device__ uint32_t compact_keys(const BlockGroup &g, uint32_t *tab, const uint3
   return out;
 }
 
+// Block-path selection straight from the table (tags in tab, counts in aux),
+// k <= 256: a radix select over the sort keys (count - 1) << 24 |
+// (2^24 - 1 - id), 8-bit digits from the top, that stops at the first digit
+// where at most 256 keys reach the threshold; those keys (the k best among
+// them) are collected and sorted by one warp.  Exactly one key remains in the
+// threshold digit after the last pass (keys are distinct), so it always
+// stops by then.  Most keys have count 1: digit 0 of the first pass is
+// counted per thread, not with shared atomics.
+__device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q, uint32_t S) {
+  uint32_t *misc = r.misc;  // [0] prefix [1] pmask [2] need [3] stop [4] threshold [5] collected [6] keys >= threshold
+  const int lane = threadIdx.x & 31;
+  if (g.rank() == 0) {
+    misc[0] = 0;
+    misc[1] = 0;
+    misc[2] = static_cast<uint32_t>(a.k);
+    misc[3] = 0;
+    misc[5] = 0;
+    misc[7] = 0;  // keys above the current prefix range
+  }
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
+    g.sync();
+    const uint32_t prefix = misc[0], pmask = misc[1];
+    uint32_t zeros = 0;
+    for (uint32_t base = 0; base < S; base += 4 * g.size()) {
+      const uint32_t i = base + 4 * g.rank();
+      if (i < S) {
+        const uint4 e = *reinterpret_cast<const uint4 *>(r.tab + i);
+        const uint2 c2 = *reinterpret_cast<const uint2 *>(r.aux + i / 2);
+        const uint32_t c[4] = {c2.x & 0xFFFFu, c2.x >> 16, c2.y & 0xFFFFu, c2.y >> 16};
+        const uint32_t t[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (t[u]) {
+            const uint32_t key = sort_key(t[u], c[u]);
+            if ((key & pmask) == prefix) {
+              const uint32_t d = (key >> shift) & 0xFFu;
+              if (pass == 0 && d == 0) ++zeros;
+              else atomicAdd(&r.hist[d], 1u);
+            }
+          }
+        }
+      }
+    }
+    if (pass == 0) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(kFull, zeros, o);
+      if (lane == 0 && zeros) atomicAdd(&r.hist[0], zeros);
+    }
+    g.sync();
+    if (g.leader_warp()) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sum += r.hist[lane * 8 + i];
+      uint32_t suf = sum;  // keys of the range with digit >= lane*8
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_down_sync(kFull, suf, o);
+        if (lane + o < 32) suf += x;
+      }
+      const uint32_t need = misc[2], above_range = misc[7];
+      const uint32_t ball = __ballot_sync(kFull, suf >= need);
+      if (ball == 0) {
+        // fewer keys in the range than needed (only when E < k, first pass): take all
+        if (lane == 0) {  // lane 0's suffix is the whole range
+          misc[4] = 1u;   // every key is >= 1 (ids < 2^24 - 1)
+          misc[6] = above_range + suf;
+          misc[3] = 1;
+        }
+      } else {
+        const int ln = 31 - __clz(ball);
+        if (lane == ln) {
+          uint32_t cum = suf - sum;
+          for (int i = 7; i >= 0; --i) {
+            const uint32_t h = r.hist[lane * 8 + i];
+            if (cum + h >= need) {
+              const uint32_t d = static_cast<uint32_t>(lane * 8 + i);
+              const uint32_t reach = above_range + cum + h;  // keys >= the bucket's lowest key
+              misc[0] = prefix | (d << shift);
+              misc[1] = pmask | (0xFFu << shift);
+              misc[2] = need - cum;
+              misc[7] = above_range + cum;
+              if (reach <= 256 || shift == 0) {
+                misc[4] = prefix | (d << shift);
+                misc[6] = reach;
+                misc[3] = 1;
+              }
+              break;
+            }
+            cum += h;
+          }
+        }
+      }
+    }
+    g.sync();
+    if (misc[3]) break;
+  }
+  const uint32_t thr = misc[4], nsel = misc[6];
+  for (uint32_t base = 0; base < S; base += 4 * g.size()) {
+    const uint32_t i = base + 4 * g.rank();
+    if (i < S) {
+      const uint4 e = *reinterpret_cast<const uint4 *>(r.tab + i);
+      const uint2 c2 = *reinterpret_cast<const uint2 *>(r.aux + i / 2);
+      const uint32_t c[4] = {c2.x & 0xFFFFu, c2.x >> 16, c2.y & 0xFFFFu, c2.y >> 16};
+      const uint32_t t[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (t[u]) {
+          const uint32_t key = sort_key(t[u], c[u]);
+          if (key >= thr) r.hist[atomicAdd(&misc[5], 1u)] = key;
+        }
+      }
+    }
+  }
+  g.sync();
+  if (threadIdx.x < 32) warp_sort_winners(a, r.hist, nsel, q);
+  g.sync();
+}
+
 __device__ __forceinline__ unsigned long long claim_query(const QArgs &a) {
   unsigned long long q = 0;
   if ((threadIdx.x & 31) == 0) q = atomicAdd(a.q_counter, 1ULL);
@@ -712,7 +937,7 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
 __global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int all_queries, int tier) {
   extern __shared__ uint32_t smem[];
   const BlockGroup g;
-  const Region r = carve(smem, a);
+  const Region r = carve_big(smem, a);
   const int64_t count = all_queries ? a.nq : static_cast<int64_t>(*a.over_count);
   for (int64_t h = blockIdx.x; h < count; h += gridDim.x) {
     int64_t q;
@@ -723,10 +948,7 @@ __global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int 
       if (v >= 0) continue;
       q = -v - 1;
     }
-    uint32_t keys[1], s[1], e[1];
-    load_query_keys<1>(g, a, q, keys);  // blockDim >= L: one table per thread
-    load_ranges<1>(g, a, keys, s, e);
-    const uint32_t M = build_ranges<1>(g, a, r.pre[0], r.sb[0], s, e);
+    const uint32_t M = build_streams(g, a, r, q);
     const uint32_t S = big_table_size(M);
     const bool defer = tier == 1 && S > a.table_words;
     if (tier == 1 && threadIdx.x == 0 && (defer || all_queries)) a.overflow[h] = defer ? -q - 1 : q;
@@ -735,12 +957,20 @@ __global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int 
     } else if (M == 0) {
       write_empty(g, a, q);
     } else {
+      const int warp = threadIdx.x >> 5;
+      const uint32_t ntab = a.L > static_cast<uint32_t>(warp) ? (a.L - warp + kBigWarps - 1) / kBigWarps : 0;
+      const uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
+      const uint32_t nbatch = (r.misc[9] + 32 * kBatch - 1) / (32 * kBatch);
       int32_t ids[kBatch];
       uint32_t cur = 0;
-      load_ids(g, a, r.pre[0], r.sb[0], M, 0, cur, ids);
-      count_phase_block(g, a, r, r.pre[0], r.sb[0], q, M, ids, S);
-      const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
-      select_phase(g, a, r, q, r.tab, E);
+      load_stream_ids(a, wp, r.off + warp * kMaxTabPerWarp, wp[ntab], 0, cur, ids);
+      count_phase_block(g, a, r, q, nbatch, ids, cur, S);
+      if (a.k <= 256) {
+        select_from_table(g, a, r, q, S);
+      } else {
+        const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
+        select_phase(g, a, r, q, r.tab, E);
+      }
     }
     g.sync();
   }
@@ -832,7 +1062,7 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
   const uint32_t tw1 = need < kBigTable ? need : kBigTable;
   for (int tier = 1; tier <= (need > tw1 ? 2 : 1); ++tier) {
     a.table_words = tier == 1 ? tw1 : need;
-    a.region_words = region_words(a);
+    a.region_words = big_region_words(a);
     const size_t smem_b = static_cast<size_t>(a.region_words) * sizeof(uint32_t);
     if (cudaFuncSetAttribute(query_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem_b)) != cudaSuccess)

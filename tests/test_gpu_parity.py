@@ -179,6 +179,8 @@ QUERY_CASES = [
     ("url_like_batched", 20_000, dict(range_bits=8, K=1), 200, 64),
     # k > 256 with second-tier queries: every query on the block path, block bitonic sort
     ("url_like_batched", 20_000, dict(range_bits=7, K=1), 300, 0),
+    # block path with fewer distinct candidates than k (every candidate is output, then padding)
+    ("tiny_plain", 3_000, dict(range_bits=9, R=8), 100, 64),
 ]
 
 
