@@ -53,6 +53,7 @@ constexpr int kQWarps = 8;  // warps per block, warp kernel
 constexpr int kBigThreads = 512;
 constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kMaxTabPerWarp = 256 / kBigWarps;  // L <= 256
+constexpr uint32_t kListCap = 2048;  // keys a block-path selection may gather before its last passes
 constexpr uint32_t kBigTable = 16384;  // slots of the first big tier's table (64 KB)
 constexpr int kBatch = 8;   // candidate ids a thread loads before counting them
 
@@ -100,9 +101,10 @@ struct BlockGroup {
 // query's bucket ranges while the current query still uses its own.
 struct Region {
   uint32_t *tab, *aux, *pre[2], *sb[2], *hist, *sel, *misc;
-  // block path only: per-table reservoir sizes and segment starts, and each
-  // warp's candidate stream (table starts in the stream, element offsets)
-  uint32_t *mt, *sbk, *wpre;
+  // block path only: per-table reservoir sizes and segment starts, each
+  // warp's candidate stream (table starts in the stream, element offsets),
+  // and the list of keys gathered by the selection
+  uint32_t *mt, *sbk, *wpre, *lst;
   long long *off;
 };
 
@@ -121,7 +123,8 @@ __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
   return r;
 }
 
-// Block path: [tab S][aux S/2][mt 256][sbk 256][wpre 16x17 (+pad)][off 16x16 x2][hist 256][sel kp][misc 40]
+// Block path: [tab S][aux S/2][mt 256][sbk 256][wpre 16x17 (+pad)][off 16x16 x2][lst 2048][hist 256][sel kp]
+//             [misc 40]
 constexpr uint32_t kWpreWords = (kBigWarps * (kMaxTabPerWarp + 1) + 3) & ~3u;
 
 __device__ __forceinline__ Region carve_big(uint32_t *base, const QArgs &a) {
@@ -132,15 +135,16 @@ __device__ __forceinline__ Region carve_big(uint32_t *base, const QArgs &a) {
   r.sbk = r.mt + 256;
   r.wpre = r.sbk + 256;
   r.off = reinterpret_cast<long long *>(r.wpre + kWpreWords);
-  r.hist = reinterpret_cast<uint32_t *>(r.off + kBigWarps * kMaxTabPerWarp);
+  r.lst = reinterpret_cast<uint32_t *>(r.off + kBigWarps * kMaxTabPerWarp);
+  r.hist = r.lst + kListCap;
   r.sel = r.hist + 256;
   r.misc = r.sel + a.kp;
   return r;
 }
 
 uint32_t big_region_words(const QArgs &a) {
-  const uint32_t w = a.table_words + a.table_words / 2 + 512 + kWpreWords + 2 * kBigWarps * kMaxTabPerWarp + 256 +
-                     a.kp + 40;
+  const uint32_t w = a.table_words + a.table_words / 2 + 512 + kWpreWords + 2 * kBigWarps * kMaxTabPerWarp + kListCap +
+                     256 + a.kp + 40;
   return (w + 3) & ~3u;
 }
 
@@ -741,16 +745,58 @@ __device__ uint32_t compact_keys(const BlockGroup &g, uint32_t *tab, const uint3
   return out;
 }
 
-// Block-path selection straight from the table (tags in tab, counts in aux),
-// k <= 256: a radix select over the sort keys (count - 1) << 24 |
-// (2^24 - 1 - id), 8-bit digits from the top, that stops at the first digit
-// where at most 256 keys reach the threshold; those keys (the k best among
-// them) are collected and sorted by one warp.  Exactly one key remains in the
-// threshold digit after the last pass (keys are distinct), so it always
-// stops by then.  Most keys have count 1: digit 0 of the first pass is
-// counted per thread, not with shared atomics.
+// Appends key to buf at (*ctr)++ where pred holds, storing only below cap
+// (*ctr still counts every key); one shared atomic per warp.  Every lane of
+// the warp calls it.
+__device__ __forceinline__ void append_warp(uint32_t *buf, uint32_t cap, uint32_t *ctr, bool pred, uint32_t key) {
+  const uint32_t ball = __ballot_sync(kFull, pred);
+  if (ball == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(ball) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(ctr, static_cast<uint32_t>(__popc(ball)));
+  base = __shfl_sync(kFull, base, leader);
+  const uint32_t pos = base + __popc(ball & ((1u << lane) - 1u));
+  if (pred && pos < cap) buf[pos] = key;
+}
+
+// Visits the sort keys of the block-path table (tags in tab, counts in aux):
+// f(u, valid, key) for the four slots of each thread and round; every thread
+// makes the same number of calls (invalid slots included), so f may use warp
+// collectives.
+template <class F>
+__device__ __forceinline__ void for_table_keys(const Region &r, uint32_t S, F &&f) {
+  for (uint32_t base = 0; base < S; base += 4 * kBigThreads) {
+    const uint32_t i = base + 4 * threadIdx.x;
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    uint2 c2 = make_uint2(0u, 0u);
+    if (i < S) {
+      e = *reinterpret_cast<const uint4 *>(r.tab + i);
+      c2 = *reinterpret_cast<const uint2 *>(r.aux + i / 2);
+    }
+    f(0, e.x != 0, e.x ? sort_key(e.x, c2.x & 0xFFFFu) : 0u);
+    f(1, e.y != 0, e.y ? sort_key(e.y, c2.x >> 16) : 0u);
+    f(2, e.z != 0, e.z ? sort_key(e.z, c2.y & 0xFFFFu) : 0u);
+    f(3, e.w != 0, e.w ? sort_key(e.w, c2.y >> 16) : 0u);
+  }
+}
+
+// Block-path selection, k <= 256: a radix select over the sort keys
+// (count - 1) << 24 | (2^24 - 1 - id), 8-bit digits from the top, that stops
+// at the first digit where at most 256 keys reach the threshold; those keys
+// are collected and sorted by one warp, which writes the k best.  Exactly one
+// key remains in the threshold digit after the last pass (keys are
+// distinct), so it always stops by then.
+// The first pass (the count digit) reads the table: count-1 entries, nearly
+// all of them, are only tallied per thread, and the keys of entries with
+// count >= 2 are gathered into a list on the way (up to kListCap).  Later
+// passes read that list when the threshold count is >= 2 and the list is
+// complete; otherwise they read the table, and the keys reaching the
+// threshold are gathered into the list once there are at most kListCap.
 __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q, uint32_t S) {
-  uint32_t *misc = r.misc;  // [0] prefix [1] pmask [2] need [3] stop [4] threshold [5] collected [6] keys >= threshold
+  // misc: [0] prefix [1] pmask [2] need [3] stop [4] threshold [5] gathered [6] keys >= threshold
+  //       [7] keys above the prefix range
+  uint32_t *misc = r.misc;
   const int lane = threadIdx.x & 31;
   if (g.rank() == 0) {
     misc[0] = 0;
@@ -758,38 +804,47 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
     misc[2] = static_cast<uint32_t>(a.k);
     misc[3] = 0;
     misc[5] = 0;
-    misc[7] = 0;  // keys above the current prefix range
+    misc[7] = 0;
   }
+  bool listed = false;
+  uint32_t nlist = 0;
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 24 - 8 * pass;
     for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
     g.sync();
     const uint32_t prefix = misc[0], pmask = misc[1];
-    uint32_t zeros = 0;
-    for (uint32_t base = 0; base < S; base += 4 * g.size()) {
-      const uint32_t i = base + 4 * g.rank();
-      if (i < S) {
-        const uint4 e = *reinterpret_cast<const uint4 *>(r.tab + i);
-        const uint2 c2 = *reinterpret_cast<const uint2 *>(r.aux + i / 2);
-        const uint32_t c[4] = {c2.x & 0xFFFFu, c2.x >> 16, c2.y & 0xFFFFu, c2.y >> 16};
+    if (pass == 0) {
+      uint32_t ones = 0;
+      for (uint32_t base = 0; base < S; base += 4 * kBigThreads) {
+        const uint32_t i = base + 4 * threadIdx.x;
+        uint4 e = make_uint4(0u, 0u, 0u, 0u);
+        uint2 c2 = make_uint2(0u, 0u);
+        if (i < S) {
+          e = *reinterpret_cast<const uint4 *>(r.tab + i);
+          c2 = *reinterpret_cast<const uint2 *>(r.aux + i / 2);
+        }
         const uint32_t t[4] = {e.x, e.y, e.z, e.w};
+        const uint32_t c[4] = {c2.x & 0xFFFFu, c2.x >> 16, c2.y & 0xFFFFu, c2.y >> 16};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (t[u]) {
-            const uint32_t key = sort_key(t[u], c[u]);
-            if ((key & pmask) == prefix) {
-              const uint32_t d = (key >> shift) & 0xFFu;
-              if (pass == 0 && d == 0) ++zeros;
-              else atomicAdd(&r.hist[d], 1u);
-            }
-          }
+          const bool multi = t[u] != 0 && c[u] > 1;
+          if (t[u] != 0 && c[u] == 1) ++ones;
+          if (multi) atomicAdd(&r.hist[c[u] - 1], 1u);
+          append_warp(r.lst, kListCap, &misc[5], multi, multi ? sort_key(t[u], c[u]) : 0u);
         }
       }
-    }
-    if (pass == 0) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(kFull, zeros, o);
-      if (lane == 0 && zeros) atomicAdd(&r.hist[0], zeros);
+      for (int o = 16; o > 0; o >>= 1) ones += __shfl_xor_sync(kFull, ones, o);
+      if (lane == 0 && ones) atomicAdd(&r.hist[0], ones);
+    } else if (!listed) {
+      for_table_keys(r, S, [&](int, bool valid, uint32_t key) {
+        if (valid && (key & pmask) == prefix) atomicAdd(&r.hist[(key >> shift) & 0xFFu], 1u);
+      });
+    } else {
+      for (uint32_t i = g.rank(); i < nlist; i += g.size()) {
+        const uint32_t key = r.lst[i];
+        if ((key & pmask) == prefix) atomicAdd(&r.hist[(key >> shift) & 0xFFu], 1u);
+      }
     }
     g.sync();
     if (g.leader_warp()) {
@@ -819,16 +874,13 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
             const uint32_t h = r.hist[lane * 8 + i];
             if (cum + h >= need) {
               const uint32_t d = static_cast<uint32_t>(lane * 8 + i);
-              const uint32_t reach = above_range + cum + h;  // keys >= the bucket's lowest key
               misc[0] = prefix | (d << shift);
               misc[1] = pmask | (0xFFu << shift);
               misc[2] = need - cum;
               misc[7] = above_range + cum;
-              if (reach <= 256 || shift == 0) {
-                misc[4] = prefix | (d << shift);
-                misc[6] = reach;
-                misc[3] = 1;
-              }
+              misc[4] = prefix | (d << shift);  // lowest key of the threshold digit
+              misc[6] = above_range + cum + h;  // keys >= it
+              if (misc[6] <= 256 || shift == 0) misc[3] = 1;
               break;
             }
             cum += h;
@@ -837,24 +889,42 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
       }
     }
     g.sync();
-    if (misc[3]) break;
-  }
-  const uint32_t thr = misc[4], nsel = misc[6];
-  for (uint32_t base = 0; base < S; base += 4 * g.size()) {
-    const uint32_t i = base + 4 * g.rank();
-    if (i < S) {
-      const uint4 e = *reinterpret_cast<const uint4 *>(r.tab + i);
-      const uint2 c2 = *reinterpret_cast<const uint2 *>(r.aux + i / 2);
-      const uint32_t c[4] = {c2.x & 0xFFFFu, c2.x >> 16, c2.y & 0xFFFFu, c2.y >> 16};
-      const uint32_t t[4] = {e.x, e.y, e.z, e.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (t[u]) {
-          const uint32_t key = sort_key(t[u], c[u]);
-          if (key >= thr) r.hist[atomicAdd(&misc[5], 1u)] = key;
-        }
+    if (pass == 0) {
+      // the list holds every key with count >= 2 unless it overflowed
+      const uint32_t gathered = misc[5];
+      if (misc[4] >= (1u << 24) && gathered <= kListCap) {
+        listed = true;
+        nlist = gathered;
       }
     }
+    if (misc[3]) break;
+    if (!listed && misc[6] <= kListCap) {  // gather the keys >= the threshold once
+      const uint32_t thr = misc[4];
+      g.sync();
+      if (g.rank() == 0) misc[5] = 0;
+      g.sync();
+      for_table_keys(r, S, [&](int, bool valid, uint32_t key) {
+        append_warp(r.lst, kListCap, &misc[5], valid && key >= thr, key);
+      });
+      g.sync();
+      listed = true;
+      nlist = misc[5];
+    }
+  }
+  g.sync();
+  if (g.rank() == 0) misc[5] = 0;
+  g.sync();
+  const uint32_t thr = misc[4], nsel = misc[6];
+  if (listed) {
+    for (uint32_t base = 0; base < nlist; base += g.size()) {
+      const uint32_t i = base + g.rank();
+      const uint32_t key = i < nlist ? r.lst[i] : 0u;
+      append_warp(r.hist, 256u, &misc[5], i < nlist && key >= thr, key);
+    }
+  } else {
+    for_table_keys(r, S, [&](int, bool valid, uint32_t key) {
+      append_warp(r.hist, 256u, &misc[5], valid && key >= thr, key);
+    });
   }
   g.sync();
   if (threadIdx.x < 32) warp_sort_winners(a, r.hist, nsel, q);
