@@ -90,10 +90,12 @@ __device__ __noinline__ void insert8_slow(int4 x, int4 y, int nvalid, const Doph
   for (int i = 0; i < nvalid; ++i) insert_dense(c[i], a, bins, mask);
 }
 
+// The hash constants come in registers (b1, B, dim): read through `a` they
+// would be reloaded after every reduction (the asm's memory clobber).
 template <bool MASKED>
 __device__ __forceinline__ void insert8(const int4 &x, const int4 &y, int nvalid, const DophParams &a,
-                                        uint32_t a1_lo, uint32_t a1_hi, uint32_t bins_s, uint32_t *bins,
-                                        uint32_t *mask) {
+                                        uint32_t a1_lo, uint32_t a1_hi, uint64_t b1, uint32_t B, uint32_t dim,
+                                        uint32_t bins_s, uint32_t *bins, uint32_t *mask) {
   uint32_t c[8] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
                    static_cast<uint32_t>(x.w), static_cast<uint32_t>(y.x), static_cast<uint32_t>(y.y),
                    static_cast<uint32_t>(y.z), static_cast<uint32_t>(y.w)};
@@ -103,20 +105,20 @@ __device__ __forceinline__ void insert8(const int4 &x, const int4 &y, int nvalid
       if (i >= nvalid) c[i] = 0;
   }
   const uint32_t mx = max(max(max(c[0], c[1]), max(c[2], c[3])), max(max(c[4], c[5]), max(c[6], c[7])));
-  if (mx >= a.dim_u32 || (a.B & 1u)) {
+  if (mx >= dim || (B & 1u)) {
     insert8_slow(x, y, MASKED ? nvalid : 8, a, bins, mask);
     return;
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     // pi = ((a1_lo*c + b1) >> 32) + a1_hi*c;  (bin, off) = (hi, lo) of pi*B
-    const uint64_t t = static_cast<uint64_t>(a1_lo) * c[i] + a.s.b1;
+    const uint64_t t = static_cast<uint64_t>(a1_lo) * c[i] + b1;
     const uint32_t pi = static_cast<uint32_t>(t >> 32) + a1_hi * c[i];
-    const uint64_t pb = static_cast<uint64_t>(pi) * a.B;
-    uint32_t off = static_cast<uint32_t>(pb);
-    if (MASKED && i >= nvalid) off = 0xFFFFFFFFu;
-    asm volatile("red.shared.min.u32 [%0], %1;" ::"r"(bins_s + 4u * static_cast<uint32_t>(pb >> 32)), "r"(off)
-                 : "memory");
+    const uint64_t pb = static_cast<uint64_t>(pi) * B;
+    if (!MASKED || i < nvalid)
+      asm volatile("red.shared.min.u32 [%0], %1;" ::"r"(bins_s + 4u * static_cast<uint32_t>(pb >> 32)),
+                   "r"(static_cast<uint32_t>(pb))
+                   : "memory");
   }
 }
 
@@ -137,6 +139,21 @@ __device__ __forceinline__ int next_word_circular(const uint32_t (&sw)[4], uint3
   return -1;
 }
 
+// The L table addresses (keys) or the B hashes of row r, all empty (the row
+// has no non-zero, or none in range): keys 2^rb, hashes all ones.
+template <bool KEYS>
+__device__ __forceinline__ void emit_empty(const DophParams &a, int64_t r, uint32_t lane) {
+  if (KEYS) {
+    const uint32_t T = static_cast<uint32_t>(1ULL << a.rb);
+    for (uint32_t t = lane; t < a.L; t += 32) {
+      if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = T;
+      if (a.out_rm) a.out_rm[r * a.L + t] = T;
+    }
+  } else {
+    for (uint32_t j = lane; j < a.B; j += 32) a.out[r * a.B + j] = kEmptyHash;
+  }
+}
+
 template <bool KEYS>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) doph_kernel(DophParams a) {
   extern __shared__ uint32_t smem[];
@@ -145,223 +162,178 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) doph_kernel(DophParams
   uint32_t *bins = smem + warp * a.smem_words_per_warp;
   uint32_t *mask = bins + a.W * 32;
   const uint32_t B = a.B, W = a.W;
-  const uint64_t T = 1ULL << a.rb;
   const uint32_t a1_lo = static_cast<uint32_t>(a.s.a1), a1_hi = static_cast<uint32_t>(a.s.a1 >> 32);
+  const uint64_t b1 = a.s.b1;
+  const uint32_t dim = a.dim_u32;
   const uint32_t bins_s = static_cast<uint32_t>(__cvta_generic_to_shared(bins));
   const int4 zero = make_int4(0, 0, 0, 0);
   const int64_t G = a.rows_per_grab;
 
-  // Rows arrive as a stream: chunks of G rows are claimed one chunk ahead (lane
-  // 0 holds the claim until it is needed), the next row's bounds are loaded
-  // while the current row is hashed, and the last 16-byte group slot of a
-  // dense row prefetches the next dense row's first group.
-  unsigned long long claim = 0;
-  if (lane == 0) claim = atomicAdd(a.row_counter, static_cast<unsigned long long>(G));
+  // Rows are claimed G at a time from a global counter; each row's bounds are
+  // read when the row starts (the 16-byte groups of the row are prefetched
+  // one group ahead, which keeps enough loads in flight).
   int64_t cpos = 0, cend = 0;
-  auto next_row = [&]() -> int64_t {
+  for (;;) {
     if (cpos >= cend) {
-      const unsigned long long s0 = __shfl_sync(kFull, claim, 0);
-      if (s0 >= static_cast<unsigned long long>(a.n_rows)) return a.n_rows;
+      unsigned long long s0 = 0;
+      if (lane == 0) s0 = atomicAdd(a.row_counter, static_cast<unsigned long long>(G));
+      s0 = __shfl_sync(kFull, s0, 0);
+      if (s0 >= static_cast<unsigned long long>(a.n_rows)) break;
       cpos = static_cast<int64_t>(s0);
       cend = min(cpos + G, a.n_rows);
-      if (lane == 0) claim = atomicAdd(a.row_counter, static_cast<unsigned long long>(G));
     }
     const int64_t pos = cpos++;
-    return a.order ? static_cast<int64_t>(a.order[pos]) : pos;
-  };
-  auto bounds = [&](int64_t r, int64_t &st, int64_t &en) {
-    st = 0;
-    en = 0;
-    if (r < a.n_rows) {
-      st = a.row_ptr[r];
-      en = a.row_ptr[r + 1];
-    }
-  };
-  auto validate = [&](int64_t &st, int64_t &en) {
-    if (st < 0 || en < st || en > a.nnz) {
+    const int64_t r = a.order ? static_cast<int64_t>(a.order[pos]) : pos;
+    int64_t start = a.row_ptr[r], end = a.row_ptr[r + 1];
+    if (start < 0 || end < start || end > a.nnz) {
       if (lane == 0) raise_error(a.err, FLASH_DEVERR_ROW_PTR);
-      st = en = 0;
+      start = end = 0;
     }
-  };
-  auto is_dense = [&](int64_t st, int64_t en) { return en - st > static_cast<int64_t>(B / 2); };
-  // group g (128 int4 of the 16-byte aligned body) of the row [st, en)
-  auto load_group = [&](int64_t st, int64_t en, int64_t g, int4 &v0, int4 &v1, int4 &v2, int4 &v3) {
-    const int64_t a4 = min((st + 3) & ~static_cast<int64_t>(3), en);
-    const int64_t b4 = max(a4, en & ~static_cast<int64_t>(3));
-    const int64_t nq = (b4 - a4) >> 2;
-    const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
-    const int64_t q0 = (g << 7) + lane;
-    v0 = q0 < nq ? __ldcs(body + q0) : zero;
-    v1 = q0 + 32 < nq ? __ldcs(body + q0 + 32) : zero;
-    v2 = q0 + 64 < nq ? __ldcs(body + q0 + 64) : zero;
-    v3 = q0 + 96 < nq ? __ldcs(body + q0 + 96) : zero;
-  };
-
-  int64_t r = next_row(), start, end;
-  bounds(r, start, end);
-  validate(start, end);
-  int4 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
-  if (r < a.n_rows && is_dense(start, end)) load_group(start, end, 0, g0, g1, g2, g3);
-
-  while (r < a.n_rows) {
-    const int64_t rn = next_row();
-    int64_t sn, en_;
-    bounds(rn, sn, en_);  // in flight while row r is hashed
-    bool next_ready = false;
     const int64_t n = end - start;
-
     if (n == 0) {  // empty row: all-ones hashes; never inserted
-      if (KEYS) {
-        for (uint32_t t = lane; t < a.L; t += 32) {
-          if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
-          if (a.out_rm) a.out_rm[r * a.L + t] = static_cast<uint32_t>(T);
+      emit_empty<KEYS>(a, r, lane);
+      __syncwarp();
+      continue;
+    }
+
+    if (n <= static_cast<int64_t>(B / 2)) {
+      // ---- sparse row: 32 non-zeros per round, one leader per bin and round
+      for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
+      __syncwarp();
+      for (int64_t base = start; base < end; base += 32) {
+        const int64_t e = base + lane;
+        bool valid = e < end;
+        uint32_t c = valid ? static_cast<uint32_t>(a.col[e]) : 0u;
+        if (valid && c >= dim) {
+          raise_error(a.err, FLASH_DEVERR_COL_RANGE);
+          valid = false;
         }
-      } else {
-        for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = kEmptyHash;
+        uint32_t bin = 0, off = 0;
+        if (valid) bin_and_offset(c, a.s, B, bin, off);
+        const uint32_t key = valid ? bin : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(kFull, key);
+        const uint32_t mn = __reduce_min_sync(peers, off);
+        if (valid && (__ffs(peers) - 1) == static_cast<int>(lane)) {
+          const uint32_t bit = 1u << (bin & 31);
+          const uint32_t m = mask[bin >> 5];
+          bins[bin] = (m & bit) ? min(bins[bin], mn) : mn;
+          atomicOr(&mask[bin >> 5], bit);
+        }
+        __syncwarp();
       }
     } else {
-      if (!is_dense(start, end)) {
-        for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
-        __syncwarp();
-        for (int64_t base = start; base < end; base += 32) {
-          const int64_t e = base + lane;
-          bool valid = e < end;
-          uint32_t c = valid ? static_cast<uint32_t>(a.col[e]) : 0u;
-          if (valid && c >= a.dim_u32) {
-            raise_error(a.err, FLASH_DEVERR_COL_RANGE);
-            valid = false;
-          }
-          uint32_t bin = 0, off = 0;
-          if (valid) bin_and_offset(c, a.s, B, bin, off);
-          const uint32_t key = valid ? bin : 0xFFFFFFFFu;
-          const uint32_t peers = __match_any_sync(kFull, key);
-          const uint32_t mn = __reduce_min_sync(peers, off);
-          if (valid && (__ffs(peers) - 1) == static_cast<int>(lane)) {
-            const uint32_t bit = 1u << (bin & 31);
-            const uint32_t m = mask[bin >> 5];
-            bins[bin] = (m & bit) ? min(bins[bin], mn) : mn;
-            atomicOr(&mask[bin >> 5], bit);
-          }
-          __syncwarp();
-        }
-      } else {
-        for (uint32_t j = lane; j < W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
-        for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
-        __syncwarp();
-        // head up to a 16-byte boundary, 16-byte body in groups of 128 int4
-        // (4 per lane, the last group partial with masked lanes), tail
-        const int64_t a4 = min((start + 3) & ~static_cast<int64_t>(3), end);
-        const int64_t b4 = max(a4, end & ~static_cast<int64_t>(3));
-        if (start + lane < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);
-        const int64_t nq = (b4 - a4) >> 2;
-        const int64_t ngroups = (nq + 127) >> 7;
-        for (int64_t g = 0; g < ngroups; ++g) {
-          int4 n0 = zero, n1 = zero, n2 = zero, n3 = zero;
-          if (g + 1 < ngroups) {
-            load_group(start, end, g + 1, n0, n1, n2, n3);
-          } else {
-            validate(sn, en_);
-            next_ready = true;
-            if (rn < a.n_rows && is_dense(sn, en_)) load_group(sn, en_, 0, n0, n1, n2, n3);
-          }
-          const int64_t q0 = (g << 7) + lane;
-          if (q0 + 96 < nq) {  // all four int4 slots of this lane hold non-zeros
-            insert8<false>(g0, g1, 8, a, a1_lo, a1_hi, bins_s, bins, mask);
-            insert8<false>(g2, g3, 8, a, a1_lo, a1_hi, bins_s, bins, mask);
-          } else {
-            // the valid slots of a lane are a prefix: each batch has 0, 4 or 8 real non-zeros
-            const int v01 = (q0 < nq ? 4 : 0) + (q0 + 32 < nq ? 4 : 0);
-            const int v23 = (q0 + 64 < nq ? 4 : 0);
-            insert8<true>(g0, g1, v01, a, a1_lo, a1_hi, bins_s, bins, mask);
-            insert8<true>(g2, g3, v23, a, a1_lo, a1_hi, bins_s, bins, mask);
-          }
-          g0 = n0;
-          g1 = n1;
-          g2 = n2;
-          g3 = n3;
-        }
-        if (b4 + lane < end) insert_dense(static_cast<uint32_t>(a.col[b4 + lane]), a, bins, mask);
-        __syncwarp();
-        for (uint32_t w = 0; w < W; ++w) {
-          const uint32_t j = w * 32 + lane;
-          const bool ne = j < B && bins[j] != 0xFFFFFFFFu;
-          const uint32_t m = __ballot_sync(kFull, ne);
-          __syncwarp();
-          if (lane == 0) mask[w] |= m;
-        }
-        __syncwarp();
+      // ---- dense row: head up to a 16-byte boundary, 16-byte body in groups
+      // of 128 int4 (4 per lane), the last group partial, tail
+      for (uint32_t j = lane; j < W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
+      for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
+      __syncwarp();
+      const int64_t a4 = min((start + 3) & ~static_cast<int64_t>(3), end);
+      const int64_t b4 = max(a4, end & ~static_cast<int64_t>(3));
+      const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
+      const int64_t nq = (b4 - a4) >> 2, nfull = nq >> 7;
+      if (start + static_cast<int64_t>(lane) < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);
+      if (b4 + static_cast<int64_t>(lane) < end) insert_dense(static_cast<uint32_t>(a.col[b4 + lane]), a, bins, mask);
+      int4 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
+      if (nfull > 0) {
+        const int4 *p0 = body + lane;
+        g0 = __ldcs(p0);
+        g1 = __ldcs(p0 + 32);
+        g2 = __ldcs(p0 + 64);
+        g3 = __ldcs(p0 + 96);
       }
+      for (int64_t g = 0; g < nfull; ++g) {
+        int4 n0 = g0, n1 = g1, n2 = g2, n3 = g3;
+        if (g + 1 < nfull) {
+          const int4 *pn = body + ((g + 1) << 7) + lane;
+          n0 = __ldcs(pn);
+          n1 = __ldcs(pn + 32);
+          n2 = __ldcs(pn + 64);
+          n3 = __ldcs(pn + 96);
+        }
+        insert8<false>(g0, g1, 8, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
+        insert8<false>(g2, g3, 8, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
+        g0 = n0;
+        g1 = n1;
+        g2 = n2;
+        g3 = n3;
+      }
+      if ((nfull << 7) < nq) {
+        // the valid slots of a lane are a prefix: each batch has 0, 4 or 8 real non-zeros
+        const int64_t q0 = (nfull << 7) + lane;
+        g0 = q0 < nq ? __ldcs(body + q0) : zero;
+        g1 = q0 + 32 < nq ? __ldcs(body + q0 + 32) : zero;
+        g2 = q0 + 64 < nq ? __ldcs(body + q0 + 64) : zero;
+        g3 = q0 + 96 < nq ? __ldcs(body + q0 + 96) : zero;
+        const int v01 = (q0 < nq ? 4 : 0) + (q0 + 32 < nq ? 4 : 0);
+        const int v23 = (q0 + 64 < nq ? 4 : 0) + (q0 + 96 < nq ? 4 : 0);
+        insert8<true>(g0, g1, v01, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
+        insert8<true>(g2, g3, v23, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
+      }
+      __syncwarp();
+      for (uint32_t w = 0; w < W; ++w) {
+        const uint32_t j = w * 32 + lane;
+        const bool ne = j < B && bins[j] != 0xFFFFFFFFu;
+        const uint32_t m = __ballot_sync(kFull, ne);
+        if (lane == 0) mask[w] |= m;
+      }
+      __syncwarp();
+    }
 
-        // ---- densification by rotation
-        uint32_t sw[4] = {0, 0, 0, 0};
-        uint32_t filled = 0;
+    // ---- densification by rotation
+    uint32_t sw[4] = {0, 0, 0, 0};
+    uint32_t filled = 0;
 #pragma unroll
-        for (uint32_t g = 0; g < 4; ++g) {
-          const uint32_t w = 32 * g + lane;
-          const uint32_t m = (g < a.G && w < W) ? mask[w] : 0u;
-          filled += __popc(m);
-          sw[g] = __ballot_sync(kFull, m != 0);
-        }
-        filled = __reduce_add_sync(kFull, filled);
-        if (filled == 0) {  // every column was out of range (flagged): hash as an empty row
-          if (KEYS) {
-            for (uint32_t t = lane; t < a.L; t += 32) {
-              if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = static_cast<uint32_t>(T);
-              if (a.out_rm) a.out_rm[r * a.L + t] = static_cast<uint32_t>(T);
-            }
-          } else {
-            for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = kEmptyHash;
-          }
-          __syncwarp();
-        } else {
-        if (filled < B) {
-          for (uint32_t w = lane; w < W; w += 32) {
-            const int w2 = next_word_circular(sw, a.G, w + 1);
-            const uint32_t nxt = 32u * static_cast<uint32_t>(w2) + (__ffs(mask[w2]) - 1);
-            const uint32_t virt = nxt > 32u * w + 31u ? nxt : nxt + B;  // wrapped: distance counts B
-            uint32_t base = bins[nxt] + virt * kRotStep;
-            const uint32_t m = mask[w];
+    for (uint32_t g = 0; g < 4; ++g) {
+      const uint32_t w = 32 * g + lane;
+      const uint32_t m = (g < a.G && w < W) ? mask[w] : 0u;
+      filled += __popc(m);
+      sw[g] = __ballot_sync(kFull, m != 0);
+    }
+    filled = __reduce_add_sync(kFull, filled);
+    if (filled == 0) {  // every column was out of range (flagged): hash as an empty row
+      emit_empty<KEYS>(a, r, lane);
+      __syncwarp();
+      continue;
+    }
+    if (filled < B) {
+      for (uint32_t w = lane; w < W; w += 32) {
+        const int w2 = next_word_circular(sw, a.G, w + 1);
+        const uint32_t nxt = 32u * static_cast<uint32_t>(w2) + (__ffs(mask[w2]) - 1);
+        const uint32_t virt = nxt > 32u * w + 31u ? nxt : nxt + B;  // wrapped: distance counts B
+        uint32_t base = bins[nxt] + virt * kRotStep;
+        const uint32_t m = mask[w];
 #pragma unroll 8
-            for (int bit = 31; bit >= 0; --bit) {
-              const uint32_t j = 32u * w + static_cast<uint32_t>(bit);
-              if (j >= B) continue;
-              if ((m >> bit) & 1u) {
-                base = bins[j] + j * kRotStep;
-              } else {
-                bins[j] = base - j * kRotStep;
-              }
-            }
+        for (int bit = 31; bit >= 0; --bit) {
+          const uint32_t j = 32u * w + static_cast<uint32_t>(bit);
+          if (j >= B) continue;
+          if ((m >> bit) & 1u) {
+            base = bins[j] + j * kRotStep;
+          } else {
+            bins[j] = base - j * kRotStep;
           }
-          __syncwarp();
         }
-  
-        // ---- emit
-        if (KEYS) {
-          const int sh = 64 - static_cast<int>(a.rb);
-          for (uint32_t t = lane; t < a.L; t += 32) {
-            uint64_t x = 0;
-            for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
-            const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
-            if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
-            if (a.out_rm) a.out_rm[r * a.L + t] = key;
-          }
-        } else if (a.vec_out) {
-          uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
-          const uint4 *src = reinterpret_cast<const uint4 *>(bins);
-          for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
-        } else {
-          for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
-        }
-        }
+      }
+      __syncwarp();
+    }
+
+    // ---- emit
+    if (KEYS) {
+      const int sh = 64 - static_cast<int>(a.rb);
+      for (uint32_t t = lane; t < a.L; t += 32) {
+        uint64_t x = 0;
+        for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
+        const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
+        if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+        if (a.out_rm) a.out_rm[r * a.L + t] = key;
+      }
+    } else if (a.vec_out) {
+      uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
+      const uint4 *src = reinterpret_cast<const uint4 *>(bins);
+      for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
+    } else {
+      for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
     }
     __syncwarp();
-    if (!next_ready) {
-      validate(sn, en_);
-      if (rn < a.n_rows && is_dense(sn, en_)) load_group(sn, en_, 0, g0, g1, g2, g3);
-    }
-    r = rn;
-    start = sn;
-    end = en_;
   }
 }
 
