@@ -287,16 +287,17 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t id, uint32_t lg) {
 // COUNTFREQUENCY of the warp path into packed entries (S >= 2M slots).  The
 // first batch of ids is given (loaded ahead by the caller); later batches are
 // loaded here with a cursor of their own.  The slot of every new entry goes to
-// the list aux; misc[4] = E.
+// the list aux (positions from a ballot per batch slot, not from a shared
+// counter); misc[4] = E.
 __device__ void count_phase_warp(const WarpGroup &g, const QArgs &a, const Region &r, const uint32_t *pre,
                                  const uint32_t *sb, int64_t q, uint32_t M, const int32_t (&first)[kBatch]) {
   const uint32_t S = table_size(M);
   const uint32_t lg = ilog2_pow2(S);
+  const uint32_t lt = (1u << (threadIdx.x & 31)) - 1u;
   for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
-  if (g.rank() == 0) r.misc[4] = 0;
   g.sync();
   const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
-  uint32_t cursor = 0;
+  uint32_t cursor = 0, E = 0;
   int32_t idv[kBatch];
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) idv[j] = first[j];
@@ -304,29 +305,36 @@ __device__ void count_phase_warp(const WarpGroup &g, const QArgs &a, const Regio
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
       const int32_t id = idv[j];
-      if (id < 0 || id == excl) continue;
-      const uint32_t tag = (static_cast<uint32_t>(id) + 1u) << 8;
-      uint32_t h = slot_hash(id, lg);
-      for (;;) {
-        uint32_t cur = r.tab[h];
-        if (cur == 0) {
-          cur = atomicCAS(&r.tab[h], 0u, tag);
+      bool fresh = false;
+      uint32_t h = 0;
+      if (id >= 0 && id != excl) {
+        const uint32_t tag = (static_cast<uint32_t>(id) + 1u) << 8;
+        h = slot_hash(id, lg);
+        for (;;) {
+          uint32_t cur = r.tab[h];
           if (cur == 0) {
-            r.aux[atomicAdd(&r.misc[4], 1u)] = h;
+            cur = atomicCAS(&r.tab[h], 0u, tag);
+            if (cur == 0) {
+              fresh = true;
+              break;
+            }
+          }
+          if ((cur & ~0xFFu) == tag) {
+            atomicAdd(&r.tab[h], 1u);
             break;
           }
+          h = (h + 1) & (S - 1);
         }
-        if ((cur & ~0xFFu) == tag) {
-          atomicAdd(&r.tab[h], 1u);
-          break;
-        }
-        h = (h + 1) & (S - 1);
       }
+      const uint32_t ball = __ballot_sync(kFull, fresh);
+      if (fresh) r.aux[E + __popc(ball & lt)] = h;
+      E += __popc(ball);
     }
     base += kBatch * g.size();
     if (base >= M) break;
     load_ids(g, a, pre, sb, M, base, cursor, idv);
   }
+  if (g.rank() == 0) r.misc[4] = E;
   g.sync();
 }
 
@@ -620,6 +628,13 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
   uint32_t *misc = r.misc;  // [0]=prefix [1]=pmask [2]=need [3]=done [5]=nsel
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
+  if constexpr (G::kIsWarp) {
+    if (E <= static_cast<uint32_t>(a.k)) {  // every key wins: sort them where they are
+      warp_sort_winners(a, keys, E, q);
+      g.sync();
+      return;
+    }
+  }
   uint32_t thr = 1;  // E <= k: every key is selected
   if (E > static_cast<uint32_t>(a.k)) {
     if (g.rank() == 0) {
@@ -679,17 +694,33 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
   }
 
   // ---- collect the winners (exactly min(k, E) keys are >= thr)
-  if (g.rank() == 0) misc[5] = 0;
-  g.sync();
-  for (uint32_t i = g.rank(); i < E; i += g.size()) {
-    const uint32_t key = keys[i];
-    if (key >= thr) {
-      const uint32_t pos = atomicAdd(&misc[5], 1u);
-      if (pos < a.kp) r.sel[pos] = key;
+  uint32_t nsel;
+  if constexpr (G::kIsWarp) {
+    uint32_t n = 0;
+    for (uint32_t base = 0; base < E; base += 32) {
+      const uint32_t i = base + lane;
+      const uint32_t key = i < E ? keys[i] : 0u;
+      const bool win = i < E && key >= thr;
+      const uint32_t ball = __ballot_sync(kFull, win);
+      const uint32_t pos = n + __popc(ball & lt);
+      if (win && pos < a.kp) r.sel[pos] = key;
+      n += __popc(ball);
     }
+    g.sync();
+    nsel = n < a.kp ? n : a.kp;
+  } else {
+    if (g.rank() == 0) misc[5] = 0;
+    g.sync();
+    for (uint32_t i = g.rank(); i < E; i += g.size()) {
+      const uint32_t key = keys[i];
+      if (key >= thr) {
+        const uint32_t pos = atomicAdd(&misc[5], 1u);
+        if (pos < a.kp) r.sel[pos] = key;
+      }
+    }
+    g.sync();
+    nsel = misc[5] < a.kp ? misc[5] : a.kp;
   }
-  g.sync();
-  const uint32_t nsel = misc[5] < a.kp ? misc[5] : a.kp;
   if constexpr (G::kIsWarp) {
     warp_sort_winners(a, r.sel, nsel, q);
   } else if (a.kp <= 256) {  // one warp sorts the winners in registers
