@@ -154,8 +154,10 @@ __device__ __forceinline__ void emit_empty(const DophParams &a, int64_t r, uint3
   }
 }
 
+// Four blocks (32 warps) per SM: the loop is latency-bound, and 32 warps beat
+// 24 with more registers (measured; five blocks spill).
 template <bool KEYS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) doph_kernel(DophParams a) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams a) {
   extern __shared__ uint32_t smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
