@@ -16,10 +16,10 @@
 //       agree on the round's minimum with __match_any_sync /
 //       __reduce_min_sync and one leader per bin updates it, so neither the
 //       bins nor any atomic on them is needed.
-// Densification (rotation): lane l owns bitmap words l, l+32, ...; it finds
-// the first non-empty bin after its word (ballot summary of non-empty
-// words) and sweeps its word downwards, writing every empty bin j as
-// v[src] + (src - j) * 0x9E3779B9 = (v[src] + src*C) - j*C.
+// Densification (rotation): word by word, lane l takes bin 32w + l; an empty
+// bin j becomes v[src] + (src - j) * 0x9E3779B9, src the first non-empty bin
+// after j, circularly (found from the word bitmap and a ballot summary of the
+// non-empty words).
 // Emit: the B hashes (coalesced, 16-byte stores when aligned) or the L keys.
 #include <cuda_runtime.h>
 
@@ -298,21 +298,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
       continue;
     }
     if (filled < B) {
-      for (uint32_t w = lane; w < W; w += 32) {
-        const int w2 = next_word_circular(sw, a.G, w + 1);
-        const uint32_t nxt = 32u * static_cast<uint32_t>(w2) + (__ffs(mask[w2]) - 1);
-        const uint32_t virt = nxt > 32u * w + 31u ? nxt : nxt + B;  // wrapped: distance counts B
-        uint32_t base = bins[nxt] + virt * kRotStep;
+      // word by word, lane l takes bin 32w + l: the words and the next non-empty
+      // word are warp-uniform (broadcast reads), bins are consecutive per lane
+      // (no bank conflicts).  An empty bin j copies the first non-empty bin
+      // after it, circularly: v[j] = v[src] + (src - j) * C, src past B when
+      // it wrapped.  Only empty bins are written and only non-empty ones read.
+      for (uint32_t w = 0; w < W; ++w) {
         const uint32_t m = mask[w];
-#pragma unroll 8
-        for (int bit = 31; bit >= 0; --bit) {
-          const uint32_t j = 32u * w + static_cast<uint32_t>(bit);
-          if (j >= B) continue;
-          if ((m >> bit) & 1u) {
-            base = bins[j] + j * kRotStep;
-          } else {
-            bins[j] = base - j * kRotStep;
-          }
+        if (m == 0xFFFFFFFFu) continue;
+        const uint32_t j = 32u * w + lane;
+        const int w2 = next_word_circular(sw, a.G, w + 1);
+        const uint32_t m2 = mask[w2];
+        if (j < B && !((m >> lane) & 1u)) {
+          const uint32_t hi = lane == 31 ? 0u : (m >> (lane + 1)) << (lane + 1);
+          const uint32_t src = hi ? 32u * w + (__ffs(hi) - 1) : 32u * static_cast<uint32_t>(w2) + (__ffs(m2) - 1);
+          const uint32_t virt = src > j ? src : src + B;  // wrapped: distance counts B
+          bins[j] = bins[src] + (virt - j) * kRotStep;
         }
       }
       __syncwarp();
@@ -410,8 +411,11 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.row_counter = L.row_counter;
   a.order = L.order;
   const double avg = L.n_rows > 0 ? static_cast<double>(L.nnz) / static_cast<double>(L.n_rows) : 1.0;
+  // short rows are claimed several at a time; at most 16, so that the rows in
+  // flight stay few enough for their table-major keys to meet in L2 (64 per
+  // claim cost the L = 256 shape half its speed in read-modify-writes)
   uint32_t g = static_cast<uint32_t>(2048.0 / (avg + 16.0) + 1.0);
-  a.rows_per_grab = g < 1 ? 1 : (g > 64 ? 64 : g);
+  a.rows_per_grab = g < 1 ? 1 : (g > 16 ? 16 : g);
   if (L.rows_per_grab) a.rows_per_grab = L.rows_per_grab;
 
   if (L.n_rows == 0) return 0;
