@@ -150,9 +150,12 @@ int flash_query_noalloc(const flash_index *index, const flash_csr *q, int32_t k,
 int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_t *out_ids, int32_t *out_counts,
                     void *stream);
 
-/* Same as flash_knn_graph with every buffer in HOST memory (pinned memory
- * gives full copy speed): the call copies the CSR to the device, runs the
- * graph and copies the results back, then synchronizes `stream`.
+/* Same as flash_knn_graph with every buffer in HOST memory: the call brings
+ * the CSR to the device, runs the graph and copies the results back, then
+ * synchronizes `stream`.  Inputs in pinned memory (allocated or registered
+ * with CUDA) are read by the hashing kernel in place over the host link;
+ * other host memory is first copied to device scratch.  The inputs must not
+ * change until the call returns.
  *   row_ptr int64 [n_rows+1], col int32 [nnz] : HOST inputs
  *   out_ids, out_counts int32 [n_rows][k]     : HOST outputs */
 int flash_knn_graph_host(const flash_params *p, const int64_t *row_ptr, const int32_t *col, int64_t n_rows,

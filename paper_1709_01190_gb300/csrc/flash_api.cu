@@ -422,6 +422,18 @@ int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_
   return rc;
 }
 
+// Device address of host memory at p when the device can read it in place
+// (memory allocated or registered with CUDA, which has a device mapping);
+// null otherwise.
+const void *device_view_of_host(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA-known pointer: clear the error
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int flash_knn_graph_host(const flash_params *p, const int64_t *row_ptr, const int32_t *col, int64_t n_rows,
                          int64_t dim, int32_t k, int32_t *out_ids, int32_t *out_counts, void *stream) {
   if (int rc = check_params(p)) return rc;
@@ -432,18 +444,28 @@ int flash_knn_graph_host(const flash_params *p, const int64_t *row_ptr, const in
   if (nnz < 0 || (nnz > 0 && !col)) return FLASH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = 0;
+  // Pinned (CUDA-allocated or registered) inputs are read by the hashing kernel
+  // in place over the host link: the CSR is read exactly once, so a separate
+  // copy would only add a pass.  Other host memory is copied first.
+  const int64_t *v_rp = static_cast<const int64_t *>(device_view_of_host(row_ptr));
+  const int32_t *v_col = nnz > 0 ? static_cast<const int32_t *>(device_view_of_host(col)) : nullptr;
+  const bool in_place = v_rp && (nnz == 0 || v_col);
   {
     Arena ar;
     int64_t *d_rp = nullptr;
     int32_t *d_col = nullptr, *d_ids = nullptr, *d_cnt = nullptr;
-    ar.add(&d_rp, n_rows + 1);
-    ar.add(&d_col, nnz);
+    if (!in_place) {
+      ar.add(&d_rp, n_rows + 1);
+      ar.add(&d_col, nnz);
+    }
     ar.add(&d_ids, n_rows * k);
     ar.add(&d_cnt, n_rows * k);
     if ((rc = ar.alloc(st))) return rc;
-    rc = cuda_ok(cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n_rows + 1), cudaMemcpyHostToDevice, st));
-    if (!rc && nnz > 0) rc = cuda_ok(cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
-    flash_csr x{d_rp, d_col, nullptr, n_rows, nnz, dim};
+    if (!in_place) {
+      rc = cuda_ok(cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n_rows + 1), cudaMemcpyHostToDevice, st));
+      if (!rc && nnz > 0) rc = cuda_ok(cudaMemcpyAsync(d_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+    }
+    flash_csr x{in_place ? v_rp : d_rp, in_place ? v_col : d_col, nullptr, n_rows, nnz, dim};
     if (!rc) rc = flash_knn_graph(p, &x, k, d_ids, d_cnt, stream);
     if (!rc) rc = cuda_ok(cudaMemcpyAsync(out_ids, d_ids, sizeof(int32_t) * n_rows * k, cudaMemcpyDeviceToHost, st));
     if (!rc)

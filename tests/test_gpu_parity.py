@@ -241,8 +241,15 @@ def test_knn_graph_host_buffers_match_device():
     ids, cnt = fl.knn_graph(p, fl.DeviceCSR.from_host(c), w.k)
     hi = np.empty((c.n_rows, w.k), np.int32)
     hc = np.empty((c.n_rows, w.k), np.int32)
-    fl.flash_knn_graph_host(p, c.row_ptr, c.col, c.dim, w.k, hi, hc)
+    fl.flash_knn_graph_host(p, c.row_ptr, c.col, c.dim, w.k, hi, hc)  # pageable: copied first
     assert np.array_equal(hi, ids.cpu().numpy()) and np.array_equal(hc, cnt.cpu().numpy())
+    # pinned inputs and outputs: the CSR is read in place by the hashing kernel
+    rp = torch.from_numpy(c.row_ptr).pin_memory()
+    col = torch.from_numpy(c.col).pin_memory()
+    pi = torch.empty((c.n_rows, w.k), dtype=torch.int32).pin_memory()
+    pc = torch.empty_like(pi).pin_memory()
+    fl.flash_knn_graph_host(p, rp.numpy(), col.numpy(), c.dim, w.k, pi.numpy(), pc.numpy())
+    assert np.array_equal(pi.numpy(), ids.cpu().numpy()) and np.array_equal(pc.numpy(), cnt.cpu().numpy())
 
 
 def test_graph_is_deterministic_across_runs():
