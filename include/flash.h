@@ -69,9 +69,11 @@ typedef struct flash_params {
 } flash_params;
 
 /* A sparse matrix in CSR form; all pointers are DEVICE pointers.
- *   row_ptr : int64 [n_rows + 1], row r holds entries [row_ptr[r], row_ptr[r+1])
+ *   row_ptr : int64 [n_rows + 1], row r holds entries [row_ptr[r], row_ptr[r+1]);
+ *             8-byte aligned
  *   col     : int32 [nnz], column ids in [0, dim); order and repeats within a
- *             row do not matter (a row is the SET of its column ids, Eq. 1)
+ *             row do not matter (a row is the SET of its column ids, Eq. 1);
+ *             4-byte aligned (a misaligned pointer is FLASH_EINVAL)
  *   val     : float32 [nnz] or NULL; ignored (DOPH is set-based, Section 2.1)
  *   nnz     : row_ptr[n_rows]; bounds every read of col */
 typedef struct flash_csr {

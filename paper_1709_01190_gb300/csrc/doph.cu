@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
   const uint32_t bins_s = static_cast<uint32_t>(__cvta_generic_to_shared(bins));
   const int4 zero = make_int4(0, 0, 0, 0);
   const int64_t G = a.rows_per_grab;
+  const int64_t mis = static_cast<int64_t>((reinterpret_cast<uintptr_t>(a.col) >> 2) & 3u);
 
   // Rows are claimed G at a time from a global counter; each row's bounds are
   // read when the row starts (the 16-byte groups of the row are prefetched
@@ -229,8 +230,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
       for (uint32_t j = lane; j < W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
       for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
       __syncwarp();
-      const int64_t a4 = min((start + 3) & ~static_cast<int64_t>(3), end);
-      const int64_t b4 = max(a4, end & ~static_cast<int64_t>(3));
+      // the 16-byte aligned body, from the actual address of col (4-byte aligned,
+      // checked on the host): element e is aligned when (e + mis) % 4 == 0
+      const int64_t a4 = min(((start + mis + 3) & ~static_cast<int64_t>(3)) - mis, end);
+      const int64_t b4 = max(a4, ((end + mis) & ~static_cast<int64_t>(3)) - mis);
       const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
       const int64_t nq = (b4 - a4) >> 2, nfull = nq >> 7;
       if (start + static_cast<int64_t>(lane) < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);

@@ -127,6 +127,8 @@ int check_csr(const flash_csr *x) {
   if (!x || x->n_rows < 0 || x->nnz < 0 || x->dim < 1) return FLASH_EINVAL;
   if (x->n_rows > 0 && !x->row_ptr) return FLASH_EINVAL;
   if (x->nnz > 0 && !x->col) return FLASH_EINVAL;
+  // natural alignment of the element types (the kernels find 16-byte boundaries themselves)
+  if ((reinterpret_cast<uintptr_t>(x->row_ptr) & 7u) || (reinterpret_cast<uintptr_t>(x->col) & 3u)) return FLASH_EINVAL;
   return 0;
 }
 

@@ -70,6 +70,7 @@ extern "C" int flash_query_noalloc(const flash_index *ix, const flash_csr *q, in
   if (!ix || !q || k < 1 || k > 1024) return FLASH_EINVAL;
   if (q->n_rows < 0 || q->nnz < 0 || q->dim < 1 || (q->n_rows > 0 && !q->row_ptr) || (q->nnz > 0 && !q->col))
     return FLASH_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(q->row_ptr) & 7u) || (reinterpret_cast<uintptr_t>(q->col) & 3u)) return FLASH_EINVAL;
   if (q->n_rows > 0 && (!out_ids || !out_counts)) return FLASH_EINVAL;
   if (q->n_rows == 0) return 0;
   const flash_params *p = &ix->p;

@@ -7,6 +7,8 @@ insertion switch, bin counts that are not multiples of 4 or 32, the largest
 bin count, heavy buckets (m >> R), k beyond the candidates and the block-level
 query path.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -72,6 +74,30 @@ def test_doph_hashes_adversarial(K, L):
     exp = oracle.doph(c.row_ptr, c.col, K, L, p.seed)
     assert np.array_equal(got, exp)
     assert fl.flash_device_error() == 0
+
+
+def test_doph_column_array_not_16_byte_aligned():
+    """A column array starting 4, 8 or 12 bytes past a 16-byte boundary (a slice): the
+    kernels find each row's 16-byte body from the actual address; a pointer that is not
+    even 4-byte aligned is rejected on the host."""
+    w = synth.WORKLOADS["webspam_like"].scaled(600)
+    c = synth.generate(w.data.replace(with_val=False))
+    p = fl.FlashParams(4, 64, 8, 12, 7)
+    exp = oracle.doph(c.row_ptr, c.col, p.K, p.L, p.seed)
+    for shift in (1, 2, 3):
+        big = torch.zeros(c.nnz + 8, dtype=torch.int32, device="cuda")
+        big[shift:shift + c.nnz] = torch.from_numpy(c.col).cuda()
+        dev = fl.DeviceCSR(torch.from_numpy(c.row_ptr).cuda(), big[shift:shift + c.nnz], c.dim)
+        assert dev.col.data_ptr() % 16 == 4 * shift
+        got = fl.hash_rows(p, dev).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, exp), shift
+    assert fl.flash_device_error() == 0
+    raw = torch.zeros(c.nnz + 4, dtype=torch.int32, device="cuda")
+    x = fl._lib.Csr(torch.from_numpy(c.row_ptr).cuda().data_ptr(), raw.data_ptr() + 2, None, c.n_rows, int(c.nnz),
+                    int(c.dim))
+    out = torch.empty((c.n_rows, p.K * p.L), dtype=torch.int32, device="cuda")
+    rc = fl._lib.lib().flash_hash(ctypes.byref(p.c()), ctypes.byref(x), out.data_ptr(), None)
+    assert rc == 1  # FLASH_EINVAL
 
 
 def test_doph_hashes_unaligned_output_and_tail():
