@@ -154,6 +154,117 @@ __device__ __forceinline__ void emit_empty(const DophParams &a, int64_t r, uint3
   }
 }
 
+// Sparse row (n <= B/2): 32 non-zeros per round; lanes with the same bin
+// agree on the round's minimum and one leader per bin updates it.
+__device__ __forceinline__ void sparse_row(const DophParams &a, int64_t start, int64_t end, uint32_t *bins,
+                                           uint32_t *mask, uint32_t lane) {
+  for (uint32_t w = lane; w < a.W; w += 32) mask[w] = 0;
+  __syncwarp();
+  for (int64_t base = start; base < end; base += 32) {
+    const int64_t e = base + lane;
+    bool valid = e < end;
+    uint32_t c = valid ? static_cast<uint32_t>(a.col[e]) : 0u;
+    if (valid && c >= a.dim_u32) {
+      raise_error(a.err, FLASH_DEVERR_COL_RANGE);
+      valid = false;
+    }
+    uint32_t bin = 0, off = 0;
+    if (valid) bin_and_offset(c, a.s, a.B, bin, off);
+    const uint32_t key = valid ? bin : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(kFull, key);
+    const uint32_t mn = __reduce_min_sync(peers, off);
+    if (valid && (__ffs(peers) - 1) == static_cast<int>(lane)) {
+      const uint32_t bit = 1u << (bin & 31);
+      const uint32_t m = mask[bin >> 5];
+      bins[bin] = (m & bit) ? min(bins[bin], mn) : mn;
+      atomicOr(&mask[bin >> 5], bit);
+    }
+    __syncwarp();
+  }
+}
+
+// Dense row, after its non-zeros are reduced: the bitmap of non-empty bins.
+__device__ __forceinline__ void dense_mask(const DophParams &a, const uint32_t *bins, uint32_t *mask,
+                                           uint32_t lane) {
+  __syncwarp();
+  for (uint32_t w = 0; w < a.W; ++w) {
+    const uint32_t j = w * 32 + lane;
+    const bool ne = j < a.B && bins[j] != 0xFFFFFFFFu;
+    const uint32_t m = __ballot_sync(kFull, ne);
+    if (lane == 0) mask[w] |= m;
+  }
+  __syncwarp();
+}
+
+// Densification by rotation and the emit of row r (keys or hashes).
+template <bool KEYS>
+__device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint32_t *bins, const uint32_t *mask,
+                                           uint32_t lane) {
+  const uint32_t B = a.B, W = a.W;
+  uint32_t sw[4] = {0, 0, 0, 0};
+  uint32_t filled = 0;
+#pragma unroll
+  for (uint32_t g = 0; g < 4; ++g) {
+    const uint32_t w = 32 * g + lane;
+    const uint32_t m = (g < a.G && w < W) ? mask[w] : 0u;
+    filled += __popc(m);
+    sw[g] = __ballot_sync(kFull, m != 0);
+  }
+  filled = __reduce_add_sync(kFull, filled);
+  if (filled == 0) {  // every column was out of range (flagged): hash as an empty row
+    emit_empty<KEYS>(a, r, lane);
+    __syncwarp();
+    return;
+  }
+  if (filled < B) {
+    // word by word, lane l takes bin 32w + l: the words and the next non-empty
+    // word are warp-uniform (broadcast reads), bins are consecutive per lane
+    // (no bank conflicts).  An empty bin j copies the first non-empty bin
+    // after it, circularly: v[j] = v[src] + (src - j) * C, src past B when
+    // it wrapped.  Only empty bins are written and only non-empty ones read.
+    for (uint32_t w = 0; w < W; ++w) {
+      const uint32_t m = mask[w];
+      if (m == 0xFFFFFFFFu) continue;
+      const uint32_t j = 32u * w + lane;
+      const int w2 = next_word_circular(sw, a.G, w + 1);
+      const uint32_t m2 = mask[w2];
+      if (j < B && !((m >> lane) & 1u)) {
+        const uint32_t hi = lane == 31 ? 0u : (m >> (lane + 1)) << (lane + 1);
+        const uint32_t src = hi ? 32u * w + (__ffs(hi) - 1) : 32u * static_cast<uint32_t>(w2) + (__ffs(m2) - 1);
+        const uint32_t virt = src > j ? src : src + B;  // wrapped: distance counts B
+        bins[j] = bins[src] + (virt - j) * kRotStep;
+      }
+    }
+    __syncwarp();
+  }
+  if (KEYS) {
+    const int sh = 64 - static_cast<int>(a.rb);
+    for (uint32_t t = lane; t < a.L; t += 32) {
+      uint64_t x = 0;
+      for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
+      const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
+      if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+      if (a.out_rm) a.out_rm[r * a.L + t] = key;
+    }
+  } else if (a.vec_out) {
+    uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
+    const uint4 *src = reinterpret_cast<const uint4 *>(bins);
+    for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
+  } else {
+    for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
+  }
+  __syncwarp();
+}
+
+// The 16-byte aligned body [a4, a4 + 4 nq) of the row [start, end), from the
+// actual address of col (4-byte aligned, checked on the host): element e is
+// aligned when (e + mis) % 4 == 0.
+__device__ __forceinline__ void row_body(int64_t start, int64_t end, int64_t mis, int64_t &a4, int64_t &nq) {
+  a4 = min(((start + mis + 3) & ~static_cast<int64_t>(3)) - mis, end);
+  const int64_t b4 = max(a4, ((end + mis) & ~static_cast<int64_t>(3)) - mis);
+  nq = (b4 - a4) >> 2;
+}
+
 // Four blocks (32 warps) per SM: the loop is latency-bound, and 32 warps beat
 // 24 with more registers (measured; five blocks spill).
 template <bool KEYS>
@@ -174,7 +285,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
 
   // Rows are claimed G at a time from a global counter; each row's bounds are
   // read when the row starts (the 16-byte groups of the row are prefetched
-  // one group ahead, which keeps enough loads in flight).
+  // one group ahead).
   int64_t cpos = 0, cend = 0;
   for (;;) {
     if (cpos >= cend) {
@@ -200,42 +311,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
     }
 
     if (n <= static_cast<int64_t>(B / 2)) {
-      // ---- sparse row: 32 non-zeros per round, one leader per bin and round
-      for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
-      __syncwarp();
-      for (int64_t base = start; base < end; base += 32) {
-        const int64_t e = base + lane;
-        bool valid = e < end;
-        uint32_t c = valid ? static_cast<uint32_t>(a.col[e]) : 0u;
-        if (valid && c >= dim) {
-          raise_error(a.err, FLASH_DEVERR_COL_RANGE);
-          valid = false;
-        }
-        uint32_t bin = 0, off = 0;
-        if (valid) bin_and_offset(c, a.s, B, bin, off);
-        const uint32_t key = valid ? bin : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(kFull, key);
-        const uint32_t mn = __reduce_min_sync(peers, off);
-        if (valid && (__ffs(peers) - 1) == static_cast<int>(lane)) {
-          const uint32_t bit = 1u << (bin & 31);
-          const uint32_t m = mask[bin >> 5];
-          bins[bin] = (m & bit) ? min(bins[bin], mn) : mn;
-          atomicOr(&mask[bin >> 5], bit);
-        }
-        __syncwarp();
-      }
+      sparse_row(a, start, end, bins, mask, lane);
     } else {
       // ---- dense row: head up to a 16-byte boundary, 16-byte body in groups
       // of 128 int4 (4 per lane), the last group partial, tail
       for (uint32_t j = lane; j < W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
       for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
       __syncwarp();
-      // the 16-byte aligned body, from the actual address of col (4-byte aligned,
-      // checked on the host): element e is aligned when (e + mis) % 4 == 0
-      const int64_t a4 = min(((start + mis + 3) & ~static_cast<int64_t>(3)) - mis, end);
-      const int64_t b4 = max(a4, ((end + mis) & ~static_cast<int64_t>(3)) - mis);
+      int64_t a4, nq;
+      row_body(start, end, mis, a4, nq);
+      const int64_t b4 = a4 + 4 * nq;
       const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
-      const int64_t nq = (b4 - a4) >> 2, nfull = nq >> 7;
+      const int64_t nfull = nq >> 7;
       if (start + static_cast<int64_t>(lane) < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);
       if (b4 + static_cast<int64_t>(lane) < end) insert_dense(static_cast<uint32_t>(a.col[b4 + lane]), a, bins, mask);
       int4 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
@@ -274,72 +361,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
         insert8<true>(g0, g1, v01, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
         insert8<true>(g2, g3, v23, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
       }
-      __syncwarp();
-      for (uint32_t w = 0; w < W; ++w) {
-        const uint32_t j = w * 32 + lane;
-        const bool ne = j < B && bins[j] != 0xFFFFFFFFu;
-        const uint32_t m = __ballot_sync(kFull, ne);
-        if (lane == 0) mask[w] |= m;
-      }
-      __syncwarp();
+      dense_mask(a, bins, mask, lane);
     }
-
-    // ---- densification by rotation
-    uint32_t sw[4] = {0, 0, 0, 0};
-    uint32_t filled = 0;
-#pragma unroll
-    for (uint32_t g = 0; g < 4; ++g) {
-      const uint32_t w = 32 * g + lane;
-      const uint32_t m = (g < a.G && w < W) ? mask[w] : 0u;
-      filled += __popc(m);
-      sw[g] = __ballot_sync(kFull, m != 0);
-    }
-    filled = __reduce_add_sync(kFull, filled);
-    if (filled == 0) {  // every column was out of range (flagged): hash as an empty row
-      emit_empty<KEYS>(a, r, lane);
-      __syncwarp();
-      continue;
-    }
-    if (filled < B) {
-      // word by word, lane l takes bin 32w + l: the words and the next non-empty
-      // word are warp-uniform (broadcast reads), bins are consecutive per lane
-      // (no bank conflicts).  An empty bin j copies the first non-empty bin
-      // after it, circularly: v[j] = v[src] + (src - j) * C, src past B when
-      // it wrapped.  Only empty bins are written and only non-empty ones read.
-      for (uint32_t w = 0; w < W; ++w) {
-        const uint32_t m = mask[w];
-        if (m == 0xFFFFFFFFu) continue;
-        const uint32_t j = 32u * w + lane;
-        const int w2 = next_word_circular(sw, a.G, w + 1);
-        const uint32_t m2 = mask[w2];
-        if (j < B && !((m >> lane) & 1u)) {
-          const uint32_t hi = lane == 31 ? 0u : (m >> (lane + 1)) << (lane + 1);
-          const uint32_t src = hi ? 32u * w + (__ffs(hi) - 1) : 32u * static_cast<uint32_t>(w2) + (__ffs(m2) - 1);
-          const uint32_t virt = src > j ? src : src + B;  // wrapped: distance counts B
-          bins[j] = bins[src] + (virt - j) * kRotStep;
-        }
-      }
-      __syncwarp();
-    }
-
-    // ---- emit
-    if (KEYS) {
-      const int sh = 64 - static_cast<int>(a.rb);
-      for (uint32_t t = lane; t < a.L; t += 32) {
-        uint64_t x = 0;
-        for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
-        const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
-        if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
-        if (a.out_rm) a.out_rm[r * a.L + t] = key;
-      }
-    } else if (a.vec_out) {
-      uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
-      const uint4 *src = reinterpret_cast<const uint4 *>(bins);
-      for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
-    } else {
-      for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
-    }
-    __syncwarp();
+    finish_row<KEYS>(a, r, bins, mask, lane);
   }
 }
 

@@ -76,6 +76,30 @@ def test_doph_hashes_adversarial(K, L):
     assert fl.flash_device_error() == 0
 
 
+@pytest.mark.parametrize("order", [0, 1])
+def test_doph_long_rows_every_length_class(order):
+    """Rows of every length class next to each other (empty, sparse, the sparse/dense switch,
+    one partial group, exact groups, many groups), in index order and longest first."""
+    from paper_1709_01190_gb300 import tuning
+    rng = np.random.default_rng(77)
+    dim = 1 << 20
+    lens = rng.choice([0, 1, 100, 129, 130, 511, 512, 513, 2047, 2048, 2049, 5000, 20000], 400)
+    rows = [list(rng.integers(0, dim, int(m))) for m in lens]
+    c = csr_of(rows, dim)
+    p = fl.FlashParams(4, 64, 4, 12, 0x1234)
+    tuning.set_tuning(tuning.Tuning(doph_order=order))
+    try:
+        got = u32(fl.hash_rows(p, fl.DeviceCSR.from_host(c)))
+        keys = fl.row_keys(p, fl.DeviceCSR.from_host(c)).cpu().numpy().view(np.uint32)
+    finally:
+        tuning.set_tuning(None)
+    assert np.array_equal(got, oracle.doph(c.row_ptr, c.col, p.K, p.L, p.seed))
+    ek = oracle.keys(c.row_ptr, c.col, p.K, p.L, p.range_bits, p.seed)
+    ek[:, np.diff(c.row_ptr) == 0] = 1 << p.range_bits
+    assert np.array_equal(keys, ek)
+    assert fl.flash_device_error() == 0
+
+
 def test_doph_column_array_not_16_byte_aligned():
     """A column array starting 4, 8 or 12 bytes past a 16-byte boundary (a slice): the
     kernels find each row's 16-byte body from the actual address; a pointer that is not
