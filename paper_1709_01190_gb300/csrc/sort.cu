@@ -27,7 +27,7 @@ namespace flash {
 
 namespace {
 
-constexpr int kSortWarps = 8;
+constexpr int kSortWarps = 16;  // per (table, tile) block: 16 warps of 8 ranking rounds (measured against 8 and 32)
 constexpr int kTile = 4096;         // elements per (table, tile) block, histogram and scatter
 constexpr int kMaxBinsSort = 257;   // 8-bit digit + the sentinel value
 constexpr unsigned kFull = 0xFFFFFFFFu;
