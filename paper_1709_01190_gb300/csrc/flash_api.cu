@@ -221,6 +221,10 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
   sl.tmp_ids = b.tids;
   sl.hist = b.hist;
   sl.starts = starts;
+  sl.R = p->R;
+  sl.heavy_count = b.counters + 1;
+  sl.heavy = b.heavy;
+  sl.heavy_cap = b.heavy_cap;
   if ((rc = sort_tables(b.plan, sl, st))) return rc;
   g_timer.mark("reservoir", st);
   ReservoirLaunch rl{};
@@ -234,6 +238,7 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
   rl.heavy_count = b.counters + 1;
   rl.heavy = b.heavy;
   rl.heavy_cap = b.heavy_cap;
+  rl.heavy_listed = true;
   return launch_reservoir(rl, st);
 }
 

@@ -66,6 +66,12 @@ struct SortLaunch {
   int32_t *tmp_ids;         // [L][n]
   uint32_t *hist;           // plan.hist_words
   uint32_t *starts;         // [L][2^rb + 1]
+  // optional: the buckets holding more than R points, listed while the starts
+  // are written (t << 32 | b; capacity heavy_cap); null to skip
+  uint32_t R;
+  unsigned long long *heavy_count;
+  uint64_t *heavy;
+  int64_t heavy_cap;
 };
 int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream);
 
@@ -79,6 +85,7 @@ struct ReservoirLaunch {
   unsigned long long *heavy_count;  // 8 bytes of scratch
   uint64_t *heavy;           // list of (t << 32 | b), capacity heavy_cap
   int64_t heavy_cap;
+  bool heavy_listed;         // the sort already listed the heavy buckets
 };
 int64_t reservoir_heavy_capacity(int64_t n, uint32_t L, uint32_t R, uint32_t range_bits);
 int launch_reservoir(const ReservoirLaunch &l, cudaStream_t stream);

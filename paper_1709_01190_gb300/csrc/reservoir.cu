@@ -94,12 +94,15 @@ int64_t reservoir_heavy_capacity(int64_t n, uint32_t L, uint32_t R, uint32_t ran
 int launch_reservoir(const ReservoirLaunch &l, cudaStream_t stream) {
   const uint32_t T = 1u << l.range_bits;
   if (l.n == 0) return 0;
-  if (cudaMemsetAsync(l.heavy_count, 0, sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
-  const int64_t total = static_cast<int64_t>(l.L) * T;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 16L * num_sms() * 8) blocks = 16L * num_sms() * 8;
-  heavy_buckets_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(l.starts, T, l.L, l.R, l.heavy_count,
-                                                                          l.heavy, l.heavy_cap);
+  if (!l.heavy_listed) {
+    if (cudaMemsetAsync(l.heavy_count, 0, sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
+    const int64_t total = static_cast<int64_t>(l.L) * T;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 16L * num_sms() * 8) blocks = 16L * num_sms() * 8;
+    heavy_buckets_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(l.starts, T, l.L, l.R, l.heavy_count,
+                                                                            l.heavy, l.heavy_cap);
+    count_launches(1);
+  }
   const size_t smem = sizeof(uint32_t) * l.R;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(reservoir_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -107,7 +110,7 @@ int launch_reservoir(const ReservoirLaunch &l, cudaStream_t stream) {
     return FLASH_ECUDA;
   reservoir_select_kernel<<<static_cast<unsigned>(num_sms() * 8), kResThreads, smem, stream>>>(
       l.ids, l.starts, l.n, T, l.R, l.r, l.heavy_count, l.heavy, l.heavy_cap);
-  count_launches(2);
+  count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }
 

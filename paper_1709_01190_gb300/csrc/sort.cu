@@ -235,8 +235,13 @@ size_t scatter_smem_bytes(bool first, int nb_pad) {
          sizeof(uint16_t) * kTile;
 }
 
+// Also lists the heavy buckets (more than R points) when heavy_count is set:
+// the bucket kp ending at element i holds more than R points exactly when the
+// element R + 1 places before i has the same address.
 __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skeys, int64_t n, uint32_t T,
-                                                             uint32_t *starts) {
+                                                             uint32_t *starts, uint32_t R,
+                                                             unsigned long long *heavy_count, uint64_t *heavy,
+                                                             int64_t heavy_cap) {
   const uint32_t t = blockIdx.y;
   const uint32_t *seg = skeys + static_cast<int64_t>(t) * n;
   uint32_t *st = starts + static_cast<int64_t>(t) * (static_cast<int64_t>(T) + 1);
@@ -252,6 +257,11 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
       const int64_t kc = i < n ? static_cast<int64_t>(seg[i]) : static_cast<int64_t>(T) + 1;
       lo = kp + 1;
       hi = kc < static_cast<int64_t>(T) ? kc : static_cast<int64_t>(T);
+      if (heavy_count && kp >= 0 && kp < static_cast<int64_t>(T) && kp < kc && i > static_cast<int64_t>(R) &&
+          static_cast<int64_t>(seg[i - R - 1]) == kp) {
+        const unsigned long long h = atomicAdd(heavy_count, 1ULL);
+        if (static_cast<int64_t>(h) < heavy_cap) heavy[h] = (static_cast<uint64_t>(t) << 32) | static_cast<uint64_t>(kp);
+      }
     }
     // short gaps (the common case: about n / 2^rb addresses per bucket) by the thread itself
     if (lo <= hi && hi - lo < 8) {
@@ -320,7 +330,10 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
   }
   const int64_t blocks_x = (s.n + 1 + 255) / 256;
   const dim3 g2(static_cast<unsigned>(blocks_x < 1024 ? blocks_x : 1024), s.L);
-  bucket_starts_kernel<<<g2, 256, 0, stream>>>(s.keys_out, s.n, static_cast<uint32_t>(T), s.starts);
+  if (s.heavy_count && cudaMemsetAsync(s.heavy_count, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+    return FLASH_ECUDA;
+  bucket_starts_kernel<<<g2, 256, 0, stream>>>(s.keys_out, s.n, static_cast<uint32_t>(T), s.starts, s.R,
+                                               s.heavy_count, s.heavy, s.heavy_cap);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }
