@@ -237,7 +237,9 @@ size_t scatter_smem_bytes(bool first, int nb_pad) {
 
 // Also lists the heavy buckets (more than R points) when heavy_count is set:
 // the bucket kp ending at element i holds more than R points exactly when the
-// element R + 1 places before i has the same address.
+// element R + 1 places before i has the same address.  Indices are 32-bit
+// (tables hold fewer than 2^24 points); each element is loaded once and its
+// predecessor comes from the neighbouring lane.
 __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skeys, int64_t n, uint32_t T,
                                                              uint32_t *starts, uint32_t R,
                                                              unsigned long long *heavy_count, uint64_t *heavy,
@@ -245,27 +247,28 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
   const uint32_t t = blockIdx.y;
   const uint32_t *seg = skeys + static_cast<int64_t>(t) * n;
   uint32_t *st = starts + static_cast<int64_t>(t) * (static_cast<int64_t>(T) + 1);
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nn = static_cast<uint32_t>(n);
+  const uint32_t stride = gridDim.x * blockDim.x;
   const uint64_t keep = l2_policy_keep();
-  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base <= n;
-       base += stride) {
-    const int64_t i = base + lane;
-    int64_t lo = 1, hi = 0;
-    if (i <= n) {
-      const int64_t kp = i > 0 ? static_cast<int64_t>(seg[i - 1]) : -1;
-      const int64_t kc = i < n ? static_cast<int64_t>(seg[i]) : static_cast<int64_t>(T) + 1;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base <= nn; base += stride) {
+    const uint32_t i = base + lane;
+    const uint32_t kc = i < nn ? seg[i] : T + 1;  // past the end: above every address
+    uint32_t kp = __shfl_up_sync(kFull, kc, 1);
+    if (lane == 0) kp = base > 0 ? seg[base - 1] : 0xFFFFFFFFu;  // none before the first element
+    // buckets kp + 1 .. min(kc, T) start at i (kp + 1 wraps to 0 for the first element)
+    uint32_t lo = 1, hi = 0;
+    if (i <= nn) {
       lo = kp + 1;
-      hi = kc < static_cast<int64_t>(T) ? kc : static_cast<int64_t>(T);
-      if (heavy_count && kp >= 0 && kp < static_cast<int64_t>(T) && kp < kc && i > static_cast<int64_t>(R) &&
-          static_cast<int64_t>(seg[i - R - 1]) == kp) {
+      hi = kc < T ? kc : T;
+      if (heavy_count && kp < T && kp < kc && i > R && seg[i - R - 1] == kp) {
         const unsigned long long h = atomicAdd(heavy_count, 1ULL);
-        if (static_cast<int64_t>(h) < heavy_cap) heavy[h] = (static_cast<uint64_t>(t) << 32) | static_cast<uint64_t>(kp);
+        if (static_cast<int64_t>(h) < heavy_cap) heavy[h] = (static_cast<uint64_t>(t) << 32) | kp;
       }
     }
     // short gaps (the common case: about n / 2^rb addresses per bucket) by the thread itself
     if (lo <= hi && hi - lo < 8) {
-      for (int64_t bkt = lo; bkt <= hi; ++bkt) st_l2(st + bkt, static_cast<uint32_t>(i), keep);
+      for (uint32_t bkt = lo; bkt <= hi; ++bkt) st_l2(st + bkt, i, keep);
       lo = 1;
       hi = 0;
     }
@@ -273,9 +276,9 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
     while (m) {
       const int src = __ffs(m) - 1;
       m &= m - 1;
-      const int64_t glo = __shfl_sync(kFull, lo, src), ghi = __shfl_sync(kFull, hi, src);
-      const uint32_t gi = static_cast<uint32_t>(__shfl_sync(kFull, i, src));
-      for (int64_t bkt = glo + lane; bkt <= ghi; bkt += 32) st_l2(st + bkt, gi, keep);
+      const uint32_t glo = __shfl_sync(kFull, lo, src), ghi = __shfl_sync(kFull, hi, src);
+      const uint32_t gi = __shfl_sync(kFull, i, src);
+      for (uint32_t bkt = glo + lane; bkt <= ghi; bkt += 32) st_l2(st + bkt, gi, keep);
     }
   }
 }
