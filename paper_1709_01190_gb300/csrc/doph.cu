@@ -401,7 +401,35 @@ __global__ void __launch_bounds__(256) row_class_scatter_kernel(const int64_t *r
   }
 }
 
+// 32 x 32 tiles (rows x tables): coalesced reads along the tables of a row,
+// coalesced writes along the rows of a table.
+__global__ void __launch_bounds__(256) transpose_keys_kernel(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *tm,
+                                                              int64_t ld) {
+  __shared__ uint32_t tile[32][33];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;  // rows on x (up to 2^31 - 1 blocks)
+  const uint32_t t0 = blockIdx.y * 32;
+  for (uint32_t y = threadIdx.y; y < 32; y += 8) {
+    const int64_t r = r0 + y;
+    const uint32_t t = t0 + threadIdx.x;
+    if (r < n && t < L) tile[y][threadIdx.x] = __ldcs(rm + r * L + t);
+  }
+  __syncthreads();
+  for (uint32_t y = threadIdx.y; y < 32; y += 8) {
+    const uint32_t t = t0 + y;
+    const int64_t r = r0 + threadIdx.x;
+    if (r < n && t < L) tm[static_cast<int64_t>(t) * ld + r] = tile[threadIdx.x][y];
+  }
+}
+
 }  // namespace
+
+int launch_transpose_keys(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *tm, int64_t ld, cudaStream_t stream) {
+  if (n <= 0) return 0;
+  const dim3 grid(static_cast<unsigned>((n + 31) / 32), (L + 31) / 32);
+  transpose_keys_kernel<<<grid, dim3(32, 8), 0, stream>>>(rm, n, L, tm, ld);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
+}
 
 int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t *hist40, cudaStream_t stream) {
   if (n <= 0) return 0;

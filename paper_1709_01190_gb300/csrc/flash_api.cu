@@ -173,7 +173,8 @@ struct RowOrder {
 // scratch of build: keys, sorted keys, sort ping-pong, histograms, heavy list, counters
 struct BuildScratch {
   uint32_t *keys = nullptr, *skeys = nullptr, *tkeys = nullptr, *hist = nullptr;
-  uint32_t *keys_rm = nullptr;  // row-major copy of the addresses (all-points graph only)
+  uint32_t *keys_rm = nullptr;  // row-major addresses (all-points graph; short rows: written first)
+  bool transpose = false;       // table-major keys from the row-major ones (short rows)
   int32_t *tids = nullptr;
   uint64_t *heavy = nullptr;
   unsigned long long *counters = nullptr;
@@ -183,8 +184,16 @@ struct BuildScratch {
   flash_tuning tu{};
 };
 
-void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, bool rowmajor_keys = false) {
+// Short rows (fewer non-zeros than tables): DOPH writes the keys row-major
+// only, and a tiled transpose makes the table-major copy for the sort.  Written
+// directly, the table-major keys of short rows are scattered 4-byte stores
+// whose sectors leave L2 half-filled (read-modify-write; 6.6 GB written for
+// 2 GB of keys at the kdd12-like shape); long rows amortise them.
+void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, int64_t nnz,
+                bool rowmajor_keys = false) {
   const int64_t ln = static_cast<int64_t>(p->L) * n;
+  b.transpose = nnz < static_cast<int64_t>(p->L) * n;
+  if (b.transpose) rowmajor_keys = true;
   b.tu = current_tuning();
   b.ro.plan(ar, b.tu, n);
   b.plan = make_sort_plan(p->range_bits, n, p->L);
@@ -204,10 +213,11 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
               uint32_t *starts, cudaStream_t st) {
   const int64_t n = x->n_rows;
   g_timer.mark("hash", st);
-  DophLaunch dl = doph_args(p, s, x, true, b.keys, n, b.counters, b.tu);
+  DophLaunch dl = doph_args(p, s, x, true, b.transpose ? nullptr : b.keys, n, b.counters, b.tu);
   dl.out_rowmajor = b.keys_rm;
   int rc = b.ro.apply(dl, x, st);
   if (!rc) rc = launch_doph(dl, st);
+  if (!rc && b.transpose) rc = launch_transpose_keys(b.keys_rm, n, p->L, b.keys, n, st);
   if (rc) return rc;
   g_timer.mark("sort", st);
   SortLaunch sl{};
@@ -352,7 +362,7 @@ int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, vo
   {
     Arena ar;
     BuildScratch b;
-    plan_build(ar, b, p, n);
+    plan_build(ar, b, p, n, x->nnz);
     rc = ar.alloc(st);
     if (!rc) rc = run_build(p, ix->s, x, b, ix->ids, ix->starts, st);
   }
@@ -411,7 +421,7 @@ int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_
   const Seeds s = derive_seeds(p->seed);
   Arena ar;
   BuildScratch b;
-  plan_build(ar, b, p, n, true);
+  plan_build(ar, b, p, n, x->nnz, true);
   int32_t *ids = nullptr;
   uint32_t *starts = nullptr;
   int64_t *overflow = nullptr;
@@ -524,7 +534,7 @@ size_t flash_knn_graph_scratch_bytes(const flash_params *p, int64_t n_rows) {
   if (check_params(p) || n_rows < 0) return 0;
   Arena ar;
   BuildScratch b;
-  plan_build(ar, b, p, n_rows, true);
+  plan_build(ar, b, p, n_rows, static_cast<int64_t>(p->L) * n_rows, true);  // same scratch either way
   int32_t *ids = nullptr;
   uint32_t *starts = nullptr;
   int64_t *overflow = nullptr;

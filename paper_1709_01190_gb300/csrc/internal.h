@@ -42,6 +42,8 @@ struct DophLaunch {
   const int32_t *order;             // optional row processing order (null = 0..n-1)
 };
 int launch_doph(const DophLaunch &l, cudaStream_t stream);
+// keys [n][L] (row-major) -> keys [L][ld] (table-major), tiled through shared memory
+int launch_transpose_keys(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *tm, int64_t ld, cudaStream_t stream);
 // order[0..n) = row ids, longest rows first (rows binned by log2 of their length);
 // hist40: 40 words of scratch
 int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t *hist40, cudaStream_t stream);
