@@ -79,6 +79,37 @@ flash_tuning current_tuning() {
 }
 
 // One stream-ordered allocation carved into 256-byte aligned parts.
+// Scratch comes from a stream-ordered pool per device owned by the library,
+// which keeps up to kPoolKeepBytes reserved between calls: the device's
+// default pool gives memory back at every synchronization, so each call would
+// map its scratch again before its first kernel.  Under stream capture the
+// default pool is used (graph allocations come from the graph's own memory).
+constexpr uint64_t kPoolKeepBytes = 16ull << 30;
+
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(d);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = d;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    pool = nullptr;
+  } else {
+    uint64_t keep = kPoolKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  pools[d] = pool;
+  return pool;
+}
+
 class Arena {
  public:
   template <class T>
@@ -90,8 +121,13 @@ class Arena {
   int alloc(cudaStream_t s) {
     const size_t cap = g_scratch_budget.load();
     if (cap && total_ > cap) return FLASH_ENOMEM;
-    if (cudaMallocAsync(&base_, total_, s) != cudaSuccess) {
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap_status) != cudaSuccess) return FLASH_ECUDA;
+    cudaMemPool_t pool = cap_status == cudaStreamCaptureStatusNone ? scratch_pool() : nullptr;
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&base_, total_, pool, s) : cudaMallocAsync(&base_, total_, s);
+    if (e != cudaSuccess) {
       cudaGetLastError();
+      base_ = nullptr;
       return FLASH_ENOMEM;
     }
     for (auto &p : parts_) *p.first = static_cast<char *>(base_) + p.second;
