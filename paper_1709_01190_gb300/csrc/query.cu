@@ -108,14 +108,19 @@ struct Region {
   long long *off;
 };
 
+// Each pre buffer is followed by its cell index (pre_words covers both).
+__host__ __device__ __forceinline__ uint32_t pre_prefix_words(uint32_t L) { return (L + 1 + 3) & ~3u; }
+__host__ __device__ __forceinline__ uint32_t cell_words(uint32_t table_words) { return ((table_words / 8) + 3) & ~3u; }
+
 __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
   Region r;
-  const uint32_t lp = (a.L + 1 + 3) & ~3u;
+  const uint32_t lp = pre_prefix_words(a.L);
+  const uint32_t pw = lp + cell_words(a.table_words);
   r.tab = base;
   r.aux = r.tab + a.table_words;
   r.pre[0] = r.aux + a.table_words / 2;
-  r.pre[1] = r.pre[0] + lp;
-  r.sb[0] = r.pre[1] + lp;
+  r.pre[1] = r.pre[0] + pw;
+  r.sb[0] = r.pre[1] + pw;
   r.sb[1] = r.sb[0] + lp;
   r.hist = r.sb[1] + lp;
   r.sel = r.hist + 256;
@@ -149,8 +154,8 @@ uint32_t big_region_words(const QArgs &a) {
 }
 
 uint32_t region_words(const QArgs &a) {
-  const uint32_t lp = (a.L + 1 + 3) & ~3u;
-  const uint32_t w = a.table_words + a.table_words / 2 + 4 * lp + 256 + a.kp + 40;
+  const uint32_t lp = pre_prefix_words(a.L);
+  const uint32_t w = a.table_words + a.table_words / 2 + 4 * lp + 2 * cell_words(a.table_words) + 256 + a.kp + 40;
   return (w + 3) & ~3u;  // every group's table starts on 16 bytes (uint4 reads)
 }
 
@@ -200,6 +205,9 @@ __device__ __forceinline__ void load_ranges(const G &g, const QArgs &a, const ui
 }
 
 // sb[t] = segment start, pre[t] = exclusive prefix of min(m_t, R); returns M = pre[L].
+// The cell index after pre: cell[c] = the table holding candidate 4c (for the
+// candidates a warp table can take), so a candidate finds its table in a step
+// or two instead of walking the prefix.
 template <int TPL, class G>
 __device__ uint32_t build_ranges(const G &g, const QArgs &a, uint32_t *pre, uint32_t *sb,
                                  const uint32_t (&s)[TPL], const uint32_t (&e)[TPL]) {
@@ -237,22 +245,35 @@ __device__ uint32_t build_ranges(const G &g, const QArgs &a, uint32_t *pre, uint
     if (lane == 31) pre[a.L] = inc;
   }
   g.sync();
+  uint32_t *cell = pre + pre_prefix_words(a.L);
+  const uint32_t ncell = cell_words(a.table_words);
+#pragma unroll
+  for (int i = 0; i < TPL; ++i) {
+    const uint32_t t = g.rank() + i * g.size();
+    if (t < a.L) {
+      const uint32_t c1 = min((pre[t + 1] + 3) >> 2, ncell);
+      for (uint32_t c = (pre[t] + 3) >> 2; c < c1; ++c) cell[c] = t;
+    }
+  }
+  g.sync();
   return pre[a.L];
 }
 
 // Candidate ids base + j*size + rank (j < kBatch) of the ranges (pre, sb); -1 past M.
-// A thread's candidate index only grows, so `cursor` walks the tables forward.
+// The table of candidate idx comes from the cell index after pre.
 template <class G>
 __device__ __forceinline__ void load_ids(const G &g, const QArgs &a, const uint32_t *pre, const uint32_t *sb,
-                                         uint32_t M, uint32_t base, uint32_t &cursor, int32_t (&idv)[kBatch]) {
+                                         uint32_t M, uint32_t base, int32_t (&idv)[kBatch]) {
   const uint64_t keep = l2_policy_keep();
+  const uint32_t *cell = pre + pre_prefix_words(a.L);
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) {
     const uint32_t idx = base + j * g.size() + g.rank();
     idv[j] = -1;
     if (idx < M) {
-      while (pre[cursor + 1] <= idx) ++cursor;
-      idv[j] = ld_l2(a.ids + static_cast<int64_t>(cursor) * a.n + sb[cursor] + (idx - pre[cursor]), keep);
+      uint32_t t = cell[idx >> 2];
+      while (pre[t + 1] <= idx) ++t;
+      idv[j] = ld_l2(a.ids + static_cast<int64_t>(t) * a.n + sb[t] + (idx - pre[t]), keep);
     }
   }
 }
@@ -286,9 +307,8 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t id, uint32_t lg) {
 
 // COUNTFREQUENCY of the warp path into packed entries (S >= 2M slots).  The
 // first batch of ids is given (loaded ahead by the caller); later batches are
-// loaded here with a cursor of their own.  The slot of every new entry goes to
-// the list aux (positions from a ballot per batch slot, not from a shared
-// counter); misc[4] = E.
+// loaded here.  The slot of every new entry goes to the list aux (positions
+// from a ballot per batch slot, not from a shared counter); misc[4] = E.
 __device__ void count_phase_warp(const WarpGroup &g, const QArgs &a, const Region &r, const uint32_t *pre,
                                  const uint32_t *sb, int64_t q, uint32_t M, const int32_t (&first)[kBatch]) {
   const uint32_t S = table_size(M);
@@ -297,7 +317,7 @@ __device__ void count_phase_warp(const WarpGroup &g, const QArgs &a, const Regio
   for (uint32_t i = g.rank(); i < S; i += g.size()) r.tab[i] = 0;
   g.sync();
   const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
-  uint32_t cursor = 0, E = 0;
+  uint32_t E = 0;
   int32_t idv[kBatch];
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) idv[j] = first[j];
@@ -332,7 +352,7 @@ __device__ void count_phase_warp(const WarpGroup &g, const QArgs &a, const Regio
     }
     base += kBatch * g.size();
     if (base >= M) break;
-    load_ids(g, a, pre, sb, M, base, cursor, idv);
+    load_ids(g, a, pre, sb, M, base, idv);
   }
   if (g.rank() == 0) r.misc[4] = E;
   g.sync();
@@ -989,8 +1009,7 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
   uint32_t *pre_c = r.pre[0], *sb_c = r.sb[0], *pre_n = r.pre[1], *sb_n = r.sb[1];
   uint32_t M = build_ranges<TPL>(g, a, pre_c, sb_c, s, e);
   int32_t ids[kBatch];
-  uint32_t cur0 = 0;
-  load_ids(g, a, pre_c, sb_c, table_size(M) <= a.table_words ? M : 0, 0, cur0, ids);
+  load_ids(g, a, pre_c, sb_c, table_size(M) <= a.table_words ? M : 0, 0, ids);
 
   while (q < nq) {
     // the next query's bucket ranges are in flight while this one is counted
@@ -1004,8 +1023,7 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
     uint32_t keys_n2[TPL];
     load_query_keys<TPL>(g, a, static_cast<int64_t>(qn2), keys_n2);
     const uint32_t Mn = build_ranges<TPL>(g, a, pre_n, sb_n, sn, en);
-    uint32_t curn = 0;
-    load_ids(g, a, pre_n, sb_n, table_size(Mn) <= a.table_words ? Mn : 0, 0, curn, ids);
+    load_ids(g, a, pre_n, sb_n, table_size(Mn) <= a.table_words ? Mn : 0, 0, ids);
 
     if (M == 0) {
       write_empty(g, a, static_cast<int64_t>(q));
