@@ -1012,14 +1012,17 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
   load_ids(g, a, pre_c, sb_c, table_size(M) <= a.table_words ? M : 0, 0, ids);
 
   while (q < nq) {
-    // the next query's bucket ranges are in flight while this one is counted
+    // the claim of the query after next, and the next query's bucket ranges,
+    // are in flight while this one is counted
+    unsigned long long qraw = 0;
+    if (lane == 0) qraw = atomicAdd(a.q_counter, 1ULL);
     uint32_t sn[TPL], en[TPL];
     load_ranges<TPL>(g, a, keys_n, sn, en);
     const bool fits = table_size(M) <= a.table_words;
     if (M > 0 && fits) count_phase_warp(g, a, r, pre_c, sb_c, static_cast<int64_t>(q), M, ids);
 
     // stage the next query: its ranges into the other buffer, its first ids in flight
-    const unsigned long long qn2 = claim_query(a);
+    const unsigned long long qn2 = __shfl_sync(kFull, qraw, 0);
     uint32_t keys_n2[TPL];
     load_query_keys<TPL>(g, a, static_cast<int64_t>(qn2), keys_n2);
     const uint32_t Mn = build_ranges<TPL>(g, a, pre_n, sb_n, sn, en);
