@@ -58,9 +58,10 @@ def _lib():
                                                   _I32, _I32, _P, _P]
         lib.oracle_knn_graph.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _I32, _P, _P]
         lib.oracle_address.argtypes = [_P, _U32, _U32, _U32, _U32, _U64]
+        lib.oracle_build_tables_from_keys.argtypes = [_P, _I64, _P, _I64, _U32, _U32, _U32, _U32, _U64, _P, _P]
         lib.oracle_address.restype = ctypes.c_uint32
         for f in ("oracle_hash", "oracle_keys", "oracle_build", "oracle_bucket", "oracle_kselect",
-                  "oracle_query", "oracle_query_one_streamed", "oracle_knn_graph"):
+                  "oracle_query", "oracle_query_one_streamed", "oracle_knn_graph", "oracle_build_tables_from_keys"):
             getattr(lib, f).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -209,6 +210,49 @@ def knn_graph(row_ptr, col, K, L, R, range_bits, seed, k):
     cnt = np.empty((n, k), dtype=np.int32)
     _check(_lib().oracle_knn_graph(prp, pcl if cl.size else None, n, K, L, R, range_bits, seed, k,
                                    ids.ctypes.data, cnt.ctypes.data))
+    return ids, cnt
+
+
+def build_tables_threaded(row_ptr, col, K, L, R, range_bits, seed, n_threads=None):
+    """build_tables with the addresses computed on several threads (row blocks) and the tables
+    built on several threads (each table is an independent Adding phase, Section 3.4); the
+    result equals build_tables."""
+    rp, prp = _c(row_ptr, np.int64)
+    n = rp.shape[0] - 1
+    T = 1 << range_bits
+    ks = keys(row_ptr, col, K, L, range_bits, seed, n_threads)
+    tables = np.empty((L, T, R), dtype=np.int32)
+    counts = np.empty((L, T), dtype=np.uint32)
+    lib = _lib()
+
+    def run(t):
+        _check(lib.oracle_build_tables_from_keys(ks.ctypes.data, n, prp, n, t, t + 1, R, range_bits, seed,
+                                                 tables.ctypes.data, counts.ctypes.data))
+
+    _pmap(run, range(L))
+    return tables, counts
+
+
+def knn_graph_threaded(row_ptr, col, K, L, R, range_bits, seed, k, n_threads=None):
+    """knn_graph on several threads: build_tables_threaded, then the queries in row blocks; the
+    result equals knn_graph."""
+    rp, _ = _c(row_ptr, np.int64)
+    cl, _ = _c(col, np.int32)
+    n = rp.shape[0] - 1
+    tables, counts = build_tables_threaded(rp, cl, K, L, R, range_bits, seed, n_threads)
+    ids = np.empty((n, k), dtype=np.int32)
+    cnt = np.empty((n, k), dtype=np.int32)
+
+    def run(ab):
+        a, b = ab
+        if b > a:
+            sub_rp = rp[a:b + 1] - rp[a]
+            i, c = query(tables, counts, K, L, R, range_bits, seed, sub_rp, cl[rp[a]:rp[b]], k,
+                         exclude=np.arange(a, b, dtype=np.int32))
+            ids[a:b] = i
+            cnt[a:b] = c
+
+    _pmap(run, _chunks(n, _workers(n_threads)))
     return ids, cnt
 
 

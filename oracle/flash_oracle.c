@@ -246,6 +246,34 @@ int oracle_build(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t
   return 0;
 }
 
+/* The Adding phase of Algorithm 2 for tables t0..t1-1 only, from the table
+ * addresses already computed (keys[t * ld + p], as oracle_keys writes
+ * them): the points arrive in index order and every ADD is the one
+ * oracle_build does, so the tables equal oracle_build's.  Tables are
+ * independent (Section 3.4), which lets a driver build them on several
+ * threads.  tables / counts as in oracle_build (all L tables).            */
+int oracle_build_tables_from_keys(const uint32_t *keys, int64_t ld, const int64_t *row_ptr, int64_t n, uint32_t t0,
+                                  uint32_t t1, uint32_t R, uint32_t rb, uint64_t seed, int32_t *tables,
+                                  uint32_t *counts) {
+  uint64_t T = 1ULL << rb, z;
+  oracle_seeds_t s = make_seeds(seed);
+  int64_t p;
+  uint32_t t;
+  for (t = t0; t < t1; ++t) {
+    for (z = 0; z < T * R; ++z) tables[(uint64_t)t * T * R + z] = -1;
+    memset(counts + (uint64_t)t * T, 0, sizeof(uint32_t) * (size_t)T);
+    for (p = 0; p < n; ++p) {
+      uint32_t key;
+      uint64_t bucket;
+      if (row_ptr[p + 1] == row_ptr[p]) continue;  /* empty rows are never inserted */
+      key = keys[(int64_t)t * ld + p];
+      bucket = (uint64_t)t * T + key;
+      add(tables + bucket * R, counts + bucket, R, s.r, t, key, (int32_t)p);
+    }
+  }
+  return 0;
+}
+
 /* Algorithm 1 run on the arrival stream of one bucket only: the points p
  * (ascending) with keys_t[p] == key and a non-empty row.  This is the
  * Adding phase restricted to bucket (t, key); used to check single buckets
