@@ -141,36 +141,40 @@ def measured_peaks():
         return {}
 
 
+def _oracle_graph(w, csr, n, threaded) -> float:
+    """Seconds for the oracle's full k-NN graph over the first n rows of the matrix."""
+    import oracle
+    p = w.params
+    rp = csr.row_ptr[:n + 1]
+    col = csr.col[:int(rp[-1])]
+    fn = oracle.knn_graph_threaded if threaded else oracle.knn_graph
+    t0 = time.perf_counter()
+    fn(rp, col, p.K, p.L, p.R, p.range_bits, p.seed, w.k)
+    return time.perf_counter() - t0
+
+
+def _oracle_sample(w, csr, threaded, target):
+    """Rows n whose oracle graph takes about target seconds, and that run's time. A small first run
+    overstates the per-row cost (fixed per-table costs), so the estimate is refined until the run is
+    near the target."""
+    n = min(csr.n_rows, 2000)
+    t = _oracle_graph(w, csr, n, threaded)
+    for _ in range(3):
+        if t >= 0.6 * target or n >= csr.n_rows:
+            break
+        n = min(csr.n_rows, max(n + 1, int(n * target / max(t, 1e-3))))
+        t = _oracle_graph(w, csr, n, threaded)
+    return n, t
+
+
 def cpu_baseline(w, csr, target_s: float) -> dict:
     """The oracle on the first n rows of the same matrix: a full k-NN graph over them, on all host
     cores (addresses in row blocks, one Adding phase per table, queries in row blocks; the C
     functions are the single-threaded oracle's), and single-threaded beside it."""
     import oracle
-    p = w.params
     threads = oracle._workers(None)
-
-    def run(n, threaded):
-        rp = csr.row_ptr[:n + 1]
-        col = csr.col[:int(rp[-1])]
-        fn = oracle.knn_graph_threaded if threaded else oracle.knn_graph
-        t0 = time.perf_counter()
-        fn(rp, col, p.K, p.L, p.R, p.range_bits, p.seed, w.k)
-        return time.perf_counter() - t0
-
-    def sized(threaded, target):
-        # size the sample from timed runs; a small first run overstates the per-row cost (fixed
-        # per-table costs), so the estimate is refined until the run is near the target
-        n = min(csr.n_rows, 2000)
-        t = run(n, threaded)
-        for _ in range(3):
-            if t >= 0.6 * target or n >= csr.n_rows:
-                break
-            n = min(csr.n_rows, max(n + 1, int(n * target / max(t, 1e-3))))
-            t = run(n, threaded)
-        return n, t
-
-    n_mt, t_mt = sized(True, target_s)
-    n_st, t_st = sized(False, target_s / 3)
+    n_mt, t_mt = _oracle_sample(w, csr, True, target_s)
+    n_st, t_st = _oracle_sample(w, csr, False, target_s / 3)
     return {"value": n_mt / t_mt, "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n_mt} rows of the same matrix ({int(csr.row_ptr[n_mt])} nnz): full build + all-points "
                       f"query of those rows, C oracle on {threads} host threads, {t_mt:.1f} s",
@@ -305,16 +309,11 @@ def run_reference(args):
     csr, _, _ = host_data(w, pinned=False)
     import oracle
     p = w.params
-    # bounded sample per step: sized from a short calibration so the whole run takes a few minutes;
-    # the oracle runs on all host cores (its C functions in threads over row blocks and tables)
+    # bounded sample per step, sized so the whole run takes a few minutes; the oracle runs on all
+    # host cores (its C functions in threads over row blocks and tables)
     threads = oracle._workers(None)
-    n0 = min(csr.n_rows, 1000)
-    t0 = time.perf_counter()
-    oracle.knn_graph_threaded(csr.row_ptr[:n0 + 1], csr.col[:int(csr.row_ptr[n0])], p.K, p.L, p.R, p.range_bits,
-                              p.seed, w.k)
-    t0 = time.perf_counter() - t0
     per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
-    n = min(csr.n_rows, max(n0, int(n0 * per_step / max(t0, 1e-3))))
+    n, _ = _oracle_sample(w, csr, True, per_step)
     rp, col = csr.row_ptr[:n + 1], csr.col[:int(csr.row_ptr[n])]
     times = []
     for i in range(args.warmup + args.steps):
