@@ -206,12 +206,13 @@ struct RowOrder {
   }
 };
 
-// scratch of build: keys, sorted keys, sort ping-pong, histograms, heavy list, counters
+// scratch of build: keys, partition ping-pong, histograms, segment starts, heavy list, counters
 struct BuildScratch {
   uint32_t *keys = nullptr, *skeys = nullptr, *tkeys = nullptr, *hist = nullptr;
   uint32_t *keys_rm = nullptr;  // row-major addresses (all-points graph; short rows: written first)
   bool transpose = false;       // table-major keys from the row-major ones (short rows)
-  int32_t *tids = nullptr;
+  int32_t *tids = nullptr, *tids2 = nullptr;
+  uint32_t *seg = nullptr;
   uint64_t *heavy = nullptr;
   unsigned long long *counters = nullptr;
   int64_t heavy_cap = 0;
@@ -236,9 +237,13 @@ void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, in
   b.heavy_cap = reservoir_heavy_capacity(n, p->L, p->R, p->range_bits);
   ar.add(&b.keys, ln);
   if (rowmajor_keys) ar.add(&b.keys_rm, ln);
-  ar.add(&b.skeys, ln);
   ar.add(&b.tkeys, ln);
   ar.add(&b.tids, ln);
+  if (b.plan.passes > 1) {
+    ar.add(&b.skeys, ln);
+    ar.add(&b.tids2, ln);
+    ar.add(&b.seg, b.plan.seg_words);
+  }
   ar.add(&b.hist, b.plan.hist_words);
   ar.add(&b.heavy, b.heavy_cap);
   ar.add(&b.counters, 8);
@@ -261,12 +266,15 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
   sl.n = n;
   sl.L = p->L;
   sl.range_bits = p->range_bits;
-  sl.keys_out = b.skeys;
   sl.ids_out = ids;
   sl.tmp_keys = b.tkeys;
   sl.tmp_ids = b.tids;
+  sl.keys_out = b.skeys;
+  sl.tmp_ids2 = b.tids2;
   sl.hist = b.hist;
+  sl.seg = b.seg;
   sl.starts = starts;
+  sl.claim = b.counters + 2;
   sl.R = p->R;
   sl.heavy_count = b.counters + 1;
   sl.heavy = b.heavy;

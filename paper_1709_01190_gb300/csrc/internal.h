@@ -48,13 +48,16 @@ int launch_transpose_keys(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *t
 // hist40: 40 words of scratch
 int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t *hist40, cudaStream_t stream);
 
-// ---- K2: per-table stable radix sort of bucket addresses + bucket starts
+// ---- K2: per-table stable sort of bucket addresses + bucket starts
+// (partition by the high bits, then one warp per segment on the low bits)
 struct SortPlan {
-  int passes;
+  int lo_bits, hi_bits;   // address bits sorted per segment / by the partition
+  int passes;             // partition passes (digits of at most 8 bits)
   int shift[4], bits[4], nbins[4];
   uint32_t tile;
   int64_t tiles;          // tiles per table
   int64_t hist_words;     // L * max_nbins * tiles
+  int64_t seg_words;      // segment starts after a multi-pass partition (0 for one pass)
 };
 SortPlan make_sort_plan(uint32_t range_bits, int64_t n, uint32_t L);
 
@@ -62,12 +65,15 @@ struct SortLaunch {
   const uint32_t *keys_in;  // [L][n] bucket addresses in [0, 2^rb]; 2^rb = not inserted
   int64_t n;
   uint32_t L, range_bits;
-  uint32_t *keys_out;       // [L][n] sorted addresses
   int32_t *ids_out;         // [L][n] point ids in (address, id) order
   uint32_t *tmp_keys;       // [L][n]
   int32_t *tmp_ids;         // [L][n]
+  uint32_t *keys_out;       // [L][n], partition passes 2, 4, ... (plan.passes > 1)
+  int32_t *tmp_ids2;        // [L][n], partition passes 2, 4, ... (plan.passes > 1)
   uint32_t *hist;           // plan.hist_words
+  uint32_t *seg;            // plan.seg_words
   uint32_t *starts;         // [L][2^rb + 1]
+  unsigned long long *claim;  // 8 bytes of scratch
   // optional: the buckets holding more than R points, listed while the starts
   // are written (t << 32 | b; capacity heavy_cap); null to skip
   uint32_t R;

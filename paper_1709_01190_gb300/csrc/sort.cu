@@ -4,20 +4,30 @@
 // bucket segment is its arrival rank).
 //
 // Each table t is a segment of n addresses keys[t][0..n) (point id = index).
-// A least-significant-digit radix sort with digits of at most 8 bits sorts
-// all segments at once; the sentinel address 2^rb (rows never inserted) is
-// one extra value of the most significant digit and sorts last.  Per pass:
-//   hist    : per (table, tile) digit histogram (shared-memory atomics);
-//   scan    : per table exclusive scan of the [digit][tile] counts;
-//   scatter : per (table, tile) stable ranking -- warps take consecutive
-//             32-element rounds, __match_any_sync ranks equal digits within
-//             a round, per-warp running counts and a per-digit prefix over
-//             warps keep the tile's element order -- a stable local sort of
-//             the tile by digit in shared memory, and coalesced writes of each
-//             digit run to scan offset + position in the run.
-// Finally the bucket starts: starts[t][b] = number of addresses < b in table
-// t, for b in [0, 2^rb]; each key change writes the starts of the buckets it
-// skips: a short run by its own thread, a long run by the whole warp.
+// An address has rb bits; the sentinel 2^rb (rows never inserted) sorts last.
+// The sort runs in two stages:
+//   1. partition: a stable least-significant-digit radix sort on the high
+//      hb = rb - lo bits only (lo = min(rb, 10)), digits of at most 8 bits,
+//      so the table falls into 2^hb + 1 segments (the last one holds the
+//      sentinels).  Per pass:
+//        hist    : per (table, tile) digit histogram (shared-memory atomics);
+//        scan    : per table exclusive scan of the [digit][tile] counts;
+//        scatter : per (table, tile) stable ranking -- warps take consecutive
+//                  32-element rounds, __match_any_sync ranks equal digits
+//                  within a round, per-warp running counts and a per-digit
+//                  prefix over warps keep the tile's element order -- a stable
+//                  local sort of the tile by digit in shared memory, and
+//                  coalesced writes of each digit run to scan offset +
+//                  position in the run.
+//      With one pass the scan already holds every segment's start; with more,
+//      a boundary kernel reads them off the partitioned addresses.
+//   2. segments: one warp per segment (about n / 2^hb points) counts its 2^lo
+//      low digits in shared memory, scans them, writes the bucket starts of
+//      its 2^lo buckets and lists the buckets holding more than R points, and
+//      places every point at its bucket's offset + its rank among the equal
+//      digits before it (32-element rounds in id order, __match_any_sync).
+//      The segment of sentinels is copied as it is.
+// starts[t][b] = number of addresses < b in table t, for b in [0, 2^rb].
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -30,6 +40,8 @@ namespace {
 constexpr int kSortWarps = 16;  // per (table, tile) block: 16 warps of 8 ranking rounds (measured against 8 and 32)
 constexpr int kTile = 4096;         // elements per (table, tile) block, histogram and scatter
 constexpr int kMaxBinsSort = 257;   // 8-bit digit + the sentinel value
+constexpr int kLoBits = 10;         // low address bits sorted per segment (2^10 counters per warp)
+constexpr int kSegWarps = 8;        // warps per block of the segment kernel
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct PassArgs {
@@ -108,7 +120,7 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *hist, int64_
 // Scatter of one (table, tile) block: rank, sort the tile locally by digit
 // in shared memory (stable), then write every digit run of the tile to its
 // global place with consecutive threads on consecutive addresses.
-template <bool FIRST, bool LAST>
+template <bool FIRST>
 __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const uint32_t *keys_in, const int32_t *ids_in,
                                                                        int64_t n, PassArgs p, int64_t tiles,
                                                                        const uint32_t *offs, uint32_t *keys_out,
@@ -219,14 +231,8 @@ __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const ui
     const uint32_t key = skey[e];
     const uint32_t d = digit_of(key, p);
     const int64_t dest = seg + goff[d] + (static_cast<uint32_t>(i) - toff[d]);
-    const int32_t id = FIRST ? static_cast<int32_t>(a + e) : sid[e];
-    if (LAST) {  // final order: the ids stay in L2 for the query phase, the keys only feed the starts
-      st_l2(ids_out + dest, id, l2_policy_keep());
-      st_l2(keys_out + dest, key, l2_policy_stream());
-    } else {
-      keys_out[dest] = key;
-      ids_out[dest] = id;
-    }
+    keys_out[dest] = key;
+    ids_out[dest] = FIRST ? static_cast<int32_t>(a + e) : sid[e];
   }
 }
 
@@ -235,40 +241,31 @@ size_t scatter_smem_bytes(bool first, int nb_pad) {
          sizeof(uint16_t) * kTile;
 }
 
-// Also lists the heavy buckets (more than R points) when heavy_count is set:
-// the bucket kp ending at element i holds more than R points exactly when the
-// element R + 1 places before i has the same address.  Indices are 32-bit
-// (tables hold fewer than 2^24 points); each element is loaded once and its
-// predecessor comes from the neighbouring lane.
-__global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skeys, int64_t n, uint32_t T,
-                                                             uint32_t *starts, uint32_t R,
-                                                             unsigned long long *heavy_count, uint64_t *heavy,
-                                                             int64_t heavy_cap) {
+// Segment starts after a multi-pass partition: seg[t][s] = number of
+// addresses a of table t with (a >> shift) < s, for s in [0, S]; the addresses
+// are sorted by a >> shift, so each change of that value writes the starts of
+// the values it skips (a short run by its own thread, a long one by the warp).
+__global__ void __launch_bounds__(256) segment_starts_kernel(const uint32_t *skeys, int64_t n, uint32_t shift,
+                                                              uint32_t S, uint32_t *seg_starts) {
   const uint32_t t = blockIdx.y;
   const uint32_t *seg = skeys + static_cast<int64_t>(t) * n;
-  uint32_t *st = starts + static_cast<int64_t>(t) * (static_cast<int64_t>(T) + 1);
+  uint32_t *st = seg_starts + static_cast<int64_t>(t) * (static_cast<int64_t>(S) + 1);
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nn = static_cast<uint32_t>(n);
   const uint32_t stride = gridDim.x * blockDim.x;
-  const uint64_t keep = l2_policy_keep();
   for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base <= nn; base += stride) {
     const uint32_t i = base + lane;
-    const uint32_t kc = i < nn ? seg[i] : T + 1;  // past the end: above every address
+    const uint32_t kc = i < nn ? (seg[i] >> shift) : S + 1;  // past the end: above every value
     uint32_t kp = __shfl_up_sync(kFull, kc, 1);
-    if (lane == 0) kp = base > 0 ? seg[base - 1] : 0xFFFFFFFFu;  // none before the first element
-    // buckets kp + 1 .. min(kc, T) start at i (kp + 1 wraps to 0 for the first element)
+    if (lane == 0) kp = base > 0 ? (seg[base - 1] >> shift) : 0xFFFFFFFFu;  // none before the first element
+    // values kp + 1 .. min(kc, S) start at i (kp + 1 wraps to 0 for the first element)
     uint32_t lo = 1, hi = 0;
     if (i <= nn) {
       lo = kp + 1;
-      hi = kc < T ? kc : T;
-      if (heavy_count && kp < T && kp < kc && i > R && seg[i - R - 1] == kp) {
-        const unsigned long long h = atomicAdd(heavy_count, 1ULL);
-        if (static_cast<int64_t>(h) < heavy_cap) heavy[h] = (static_cast<uint64_t>(t) << 32) | kp;
-      }
+      hi = kc < S ? kc : S;
     }
-    // short gaps (the common case: about n / 2^rb addresses per bucket) by the thread itself
     if (lo <= hi && hi - lo < 8) {
-      for (uint32_t bkt = lo; bkt <= hi; ++bkt) st_l2(st + bkt, i, keep);
+      for (uint32_t v = lo; v <= hi; ++v) st[v] = i;
       lo = 1;
       hi = 0;
     }
@@ -278,7 +275,129 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
       m &= m - 1;
       const uint32_t glo = __shfl_sync(kFull, lo, src), ghi = __shfl_sync(kFull, hi, src);
       const uint32_t gi = __shfl_sync(kFull, i, src);
-      for (uint32_t bkt = glo + lane; bkt <= ghi; bkt += 32) st_l2(st + bkt, gi, keep);
+      for (uint32_t v = glo + lane; v <= ghi; v += 32) st[v] = gi;
+    }
+  }
+}
+
+struct SegArgs {
+  const uint32_t *pkeys;     // [L][n] addresses partitioned by their high bits
+  const int32_t *pids;       // [L][n] point ids in the same order
+  int64_t n;
+  uint32_t L, lo, hb;        // address = (segment << lo) | low digit; 2^hb regular segments + the sentinels
+  const uint32_t *seg;       // start of segment s of table t: seg[t * seg_tstride + s * seg_sstride]
+  int64_t seg_tstride, seg_sstride;
+  int32_t *ids_out;          // [L][n] point ids in (address, id) order
+  uint32_t *starts;          // [L][2^rb + 1]
+  uint32_t R;
+  unsigned long long *heavy_count;  // buckets with more than R points: (t << 32 | b), capacity heavy_cap
+  uint64_t *heavy;
+  int64_t heavy_cap;
+  unsigned long long *claim;  // segment claims (zeroed before the launch)
+};
+
+// One warp per segment: count the low digits, scan, write the bucket starts and
+// the heavy buckets, place every point (stable).  Segments are claimed from the
+// last table backwards: the partition wrote the last tables last, so their
+// addresses and ids are the ones still in L2.
+__global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a) {
+  extern __shared__ uint32_t seg_sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nb = 1u << a.lo, dmask = nb - 1u;
+  uint32_t *cnt = seg_sm + static_cast<size_t>(warp) * nb;
+  const uint32_t nseg = (1u << a.hb) + 1u;
+  const uint64_t total = static_cast<uint64_t>(a.L) * nseg;
+  const uint32_t T = 1u << (a.lo + a.hb);
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint64_t keep = l2_policy_keep();
+  for (;;) {
+    unsigned long long g = 0;
+    if (lane == 0) g = atomicAdd(a.claim, 1ULL);
+    g = __shfl_sync(kFull, g, 0);
+    if (g >= total) break;
+    g = total - 1 - g;
+    const uint32_t t = static_cast<uint32_t>(g / nseg), s = static_cast<uint32_t>(g - static_cast<uint64_t>(t) * nseg);
+    const uint32_t *sb = a.seg + static_cast<int64_t>(t) * a.seg_tstride;
+    const uint32_t so = sb[static_cast<int64_t>(s) * a.seg_sstride];
+    const uint32_t se = s + 1 < nseg ? sb[static_cast<int64_t>(s + 1) * a.seg_sstride] : static_cast<uint32_t>(a.n);
+    const int64_t tb = static_cast<int64_t>(t) * a.n;
+    const uint32_t *pk = a.pkeys + tb;
+    const int32_t *pi = a.pids + tb;
+    int32_t *out = a.ids_out + tb;
+    uint32_t *st = a.starts + static_cast<int64_t>(t) * (static_cast<int64_t>(T) + 1);
+    if (s + 1 == nseg) {  // the points never inserted: already in id order
+      if (lane == 0) st_l2(st + T, so, keep);
+      for (uint32_t i = so + lane; i < se; i += 32) st_l2(out + i, pi[i], keep);
+      continue;
+    }
+    for (uint32_t d = lane; d < nb; d += 32) cnt[d] = 0;
+    __syncwarp();
+    // count the low digits
+    {
+      uint32_t i = so + lane;
+      for (; i + 96 < se; i += 128) {
+        const uint32_t k0 = pk[i], k1 = pk[i + 32], k2 = pk[i + 64], k3 = pk[i + 96];
+        atomicAdd(&cnt[k0 & dmask], 1u);
+        atomicAdd(&cnt[k1 & dmask], 1u);
+        atomicAdd(&cnt[k2 & dmask], 1u);
+        atomicAdd(&cnt[k3 & dmask], 1u);
+      }
+      for (; i < se; i += 32) atomicAdd(&cnt[pk[i] & dmask], 1u);
+    }
+    __syncwarp();
+    // exclusive scan in place (lane owns a run of consecutive digits); heavy buckets
+    {
+      const uint32_t per = (nb + 31) / 32;
+      const uint32_t d0 = min(nb, lane * per), d1 = min(nb, d0 + per);
+      uint32_t sum = 0;
+      for (uint32_t d = d0; d < d1; ++d) {
+        const uint32_t c = cnt[d];
+        sum += c;
+        if (c > a.R && a.heavy_count) {
+          const unsigned long long h = atomicAdd(a.heavy_count, 1ULL);
+          if (static_cast<int64_t>(h) < a.heavy_cap)
+            a.heavy[h] = (static_cast<uint64_t>(t) << 32) | ((s << a.lo) | d);
+        }
+      }
+      uint32_t inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += x;
+      }
+      uint32_t run = so + inc - sum;
+      for (uint32_t d = d0; d < d1; ++d) {
+        const uint32_t c = cnt[d];
+        cnt[d] = run;
+        run += c;
+      }
+    }
+    __syncwarp();
+    for (uint32_t d = lane; d < nb; d += 32) st_l2(st + ((s << a.lo) | d), cnt[d], keep);
+    __syncwarp();
+    // place: rank among equal digits of the round, after the earlier rounds
+    for (uint32_t base = so; base < se; base += 128) {
+      uint32_t kk[4];
+      int32_t id[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        kk[r] = i < se ? pk[i] : 0u;
+        id[r] = i < se ? pi[i] : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        if (base + r * 32 >= se) break;  // warp-uniform
+        const bool valid = i < se;
+        const uint32_t d = valid ? (kk[r] & dmask) : (nb + static_cast<uint32_t>(lane));
+        const uint32_t peers = __match_any_sync(kFull, d);
+        const uint32_t before = valid ? cnt[d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0) cnt[d] = before + __popc(peers);
+        __syncwarp();
+        if (valid) st_l2(out + before + __popc(peers & lt_mask), id[r], keep);
+      }
     }
   }
 }
@@ -287,10 +406,12 @@ __global__ void __launch_bounds__(256) bucket_starts_kernel(const uint32_t *skey
 
 SortPlan make_sort_plan(uint32_t range_bits, int64_t n, uint32_t L) {
   SortPlan p{};
-  p.passes = static_cast<int>((range_bits + 7) / 8);
-  if (p.passes < 1) p.passes = 1;
-  const int base = static_cast<int>(range_bits) / p.passes, extra = static_cast<int>(range_bits) % p.passes;
-  int shift = 0, maxb = 0;
+  p.lo_bits = static_cast<int>(range_bits) < kLoBits ? static_cast<int>(range_bits) : kLoBits;
+  p.hi_bits = static_cast<int>(range_bits) - p.lo_bits;
+  p.passes = (p.hi_bits + 7) / 8;
+  if (p.passes < 1) p.passes = 1;  // hi_bits = 0: one pass still moves the sentinels last
+  const int base = p.hi_bits / p.passes, extra = p.hi_bits % p.passes;
+  int shift = p.lo_bits, maxb = 0;
   for (int i = 0; i < p.passes; ++i) {
     p.bits[i] = base + (i < extra ? 1 : 0);
     p.shift[i] = shift;
@@ -301,6 +422,7 @@ SortPlan make_sort_plan(uint32_t range_bits, int64_t n, uint32_t L) {
   p.tile = kTile;
   p.tiles = n > 0 ? (n + p.tile - 1) / p.tile : 0;
   p.hist_words = static_cast<int64_t>(L) * maxb * (p.tiles > 0 ? p.tiles : 1);
+  p.seg_words = p.passes > 1 ? static_cast<int64_t>(L) * ((1LL << p.hi_bits) + 1) : 0;
   return p;
 }
 
@@ -309,21 +431,20 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
   if (s.n == 0) {
     return cudaMemsetAsync(s.starts, 0, sizeof(uint32_t) * s.L * (T + 1), stream) == cudaSuccess ? 0 : FLASH_ECUDA;
   }
+  // 1. partition by the high bits; passes alternate between (tmp_keys, tmp_ids)
+  //    and (keys_out, tmp_ids2)
   const dim3 grid(static_cast<unsigned>(plan.tiles), s.L);
   const uint32_t *kin = s.keys_in;
   const int32_t *vin = nullptr;
   for (int pass = 0; pass < plan.passes; ++pass) {
     PassArgs pa{plan.shift[pass], plan.bits[pass], plan.nbins[pass], pass == plan.passes - 1};
-    const bool to_final = ((plan.passes - 1 - pass) % 2) == 0;
-    uint32_t *kout = to_final ? s.keys_out : s.tmp_keys;
-    int32_t *vout = to_final ? s.ids_out : s.tmp_ids;
+    uint32_t *kout = pass % 2 == 0 ? s.tmp_keys : s.keys_out;
+    int32_t *vout = pass % 2 == 0 ? s.tmp_ids : s.tmp_ids2;
     radix_hist_kernel<<<grid, 256, 0, stream>>>(kin, s.n, pa, plan.tile, plan.tiles, s.hist);
     radix_scan_kernel<<<s.L, 1024, 0, stream>>>(s.hist, static_cast<int64_t>(pa.nbins) * plan.tiles);
     const int nb_pad = (pa.nbins + 3) & ~3;
     const size_t smem = scatter_smem_bytes(pass == 0, nb_pad);
-    const bool last = pass == plan.passes - 1;
-    auto kern = pass == 0 ? (last ? radix_scatter_kernel<true, true> : radix_scatter_kernel<true, false>)
-                          : (last ? radix_scatter_kernel<false, true> : radix_scatter_kernel<false, false>);
+    auto kern = pass == 0 ? radix_scatter_kernel<true> : radix_scatter_kernel<false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
       return FLASH_ECUDA;
     kern<<<grid, kSortWarps * 32, smem, stream>>>(kin, vin, s.n, pa, plan.tiles, s.hist, kout, vout, nb_pad);
@@ -331,12 +452,54 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
     kin = kout;
     vin = vout;
   }
-  const int64_t blocks_x = (s.n + 1 + 255) / 256;
-  const dim3 g2(static_cast<unsigned>(blocks_x < 1024 ? blocks_x : 1024), s.L);
+  // 2. segment starts: from the scan of a single pass (digit s of table t at
+  //    hist[(t * nbins + s) * tiles]), else read off the partitioned addresses
+  SegArgs a{};
+  a.pkeys = kin;
+  a.pids = vin;
+  a.n = s.n;
+  a.L = s.L;
+  a.lo = static_cast<uint32_t>(plan.lo_bits);
+  a.hb = static_cast<uint32_t>(plan.hi_bits);
+  const uint32_t S = 1u << plan.hi_bits;
+  if (plan.passes == 1) {
+    a.seg = s.hist;
+    a.seg_tstride = static_cast<int64_t>(plan.nbins[0]) * plan.tiles;
+    a.seg_sstride = plan.tiles;
+  } else {
+    const int64_t blocks_x = (s.n + 1 + 255) / 256;
+    const dim3 g2(static_cast<unsigned>(blocks_x < 1024 ? blocks_x : 1024), s.L);
+    segment_starts_kernel<<<g2, 256, 0, stream>>>(kin, s.n, static_cast<uint32_t>(plan.lo_bits), S, s.seg);
+    count_launches(1);
+    a.seg = s.seg;
+    a.seg_tstride = static_cast<int64_t>(S) + 1;
+    a.seg_sstride = 1;
+  }
+  a.ids_out = s.ids_out;
+  a.starts = s.starts;
+  a.R = s.R;
+  a.heavy_count = s.heavy_count;
+  a.heavy = s.heavy;
+  a.heavy_cap = s.heavy_cap;
+  a.claim = s.claim;
+  // 3. one warp per segment
+  if (cudaMemsetAsync(s.claim, 0, sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
   if (s.heavy_count && cudaMemsetAsync(s.heavy_count, 0, sizeof(unsigned long long), stream) != cudaSuccess)
     return FLASH_ECUDA;
-  bucket_starts_kernel<<<g2, 256, 0, stream>>>(s.keys_out, s.n, static_cast<uint32_t>(T), s.starts, s.R,
-                                               s.heavy_count, s.heavy, s.heavy_cap);
+  const size_t smem = sizeof(uint32_t) * kSegWarps * (static_cast<size_t>(1) << plan.lo_bits);
+  if (cudaFuncSetAttribute(segment_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return FLASH_ECUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, segment_sort_kernel, kSegWarps * 32, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return FLASH_ECUDA;
+  const int64_t segs = static_cast<int64_t>(s.L) * (static_cast<int64_t>(S) + 1);
+  int64_t blocks = static_cast<int64_t>(per_sm) * num_sms();
+  const int64_t need = (segs + kSegWarps - 1) / kSegWarps;
+  if (blocks > need) blocks = need;
+  segment_sort_kernel<<<static_cast<unsigned>(blocks), kSegWarps * 32, smem, stream>>>(a);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }
