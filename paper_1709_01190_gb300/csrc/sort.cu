@@ -118,21 +118,20 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *hist, int64_
 }
 
 // Scatter of one (table, tile) block: rank, sort the tile locally by digit
-// in shared memory (stable), then write every digit run of the tile to its
+// into shared memory (stable), then write every digit run of the tile to its
 // global place with consecutive threads on consecutive addresses.
 template <bool FIRST>
-__global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const uint32_t *keys_in, const int32_t *ids_in,
+__global__ void __launch_bounds__(kSortWarps * 32, 3) radix_scatter_kernel(const uint32_t *keys_in, const int32_t *ids_in,
                                                                        int64_t n, PassArgs p, int64_t tiles,
                                                                        const uint32_t *offs, uint32_t *keys_out,
                                                                        int32_t *ids_out, int nb_pad) {
   extern __shared__ uint32_t sm[];
-  uint32_t *skey = sm;                                          // [kTile] keys, tile order
-  int32_t *sid = reinterpret_cast<int32_t *>(skey + kTile);     // [kTile] ids (not FIRST)
-  uint32_t *wcnt = reinterpret_cast<uint32_t *>(sid + (FIRST ? 0 : kTile));  // [kSortWarps][nb_pad]
+  uint32_t *skey = sm;                                          // [kTile] keys in digit order
+  int32_t *sid = reinterpret_cast<int32_t *>(skey + kTile);     // [kTile] ids in digit order
+  uint32_t *wcnt = reinterpret_cast<uint32_t *>(sid + kTile);   // [kSortWarps][nb_pad]
   uint32_t *wpref = wcnt + kSortWarps * nb_pad;                 // [kSortWarps][nb_pad]
   uint32_t *toff = wpref + kSortWarps * nb_pad;                 // [nb_pad] digit offset inside the tile
-  uint32_t *goff = toff + nb_pad;                               // [nb_pad] digit offset in the table
-  uint16_t *perm = reinterpret_cast<uint16_t *>(goff + nb_pad); // [kTile] tile index in digit order
+  uint32_t *gdel = toff + nb_pad;                               // [nb_pad] table offset - tile offset of a digit
   const uint32_t t = blockIdx.y;
   const int64_t ti = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const ui
   const int cnt = static_cast<int>(min(n - a, static_cast<int64_t>(kTile)));
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t *my_cnt = wcnt + warp * nb_pad;
-  for (int d = threadIdx.x; d < p.nbins; d += blockDim.x) goff[d] = offs[(static_cast<int64_t>(t) * p.nbins + d) * tiles + ti];
+  for (int d = threadIdx.x; d < p.nbins; d += blockDim.x) gdel[d] = offs[(static_cast<int64_t>(t) * p.nbins + d) * tiles + ti];
   for (int d = lane; d < p.nbins; d += 32) my_cnt[d] = 0;
   __syncwarp();
 
@@ -150,23 +149,20 @@ __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const ui
   constexpr int kRounds = kPerWarp / 32;
   uint32_t dr[kRounds];  // digit << 16 | rank among the warp's equal digits
   uint32_t kk[kRounds];
+  int32_t vv[kRounds];
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int e = warp * kPerWarp + r * 32 + lane;
     kk[r] = e < cnt ? __ldcs(keys_in + seg + a + e) : 0u;
-  }
-  if (!FIRST) {
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-      const int e = warp * kPerWarp + r * 32 + lane;
-      if (e < cnt) sid[e] = __ldcs(ids_in + seg + a + e);
-    }
+    if (FIRST)
+      vv[r] = static_cast<int32_t>(a + e);
+    else
+      vv[r] = e < cnt ? __ldcs(ids_in + seg + a + e) : 0;
   }
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const int e = warp * kPerWarp + r * 32 + lane;
     const bool valid = e < cnt;
-    if (valid) skey[e] = kk[r];
     const uint32_t d = valid ? digit_of(kk[r], p) : 0xFFFFu;
     const uint32_t peers = __match_any_sync(kFull, d);
     const uint32_t lower = peers & lt_mask;
@@ -208,37 +204,41 @@ __global__ void __launch_bounds__(kSortWarps * 32) radix_scatter_kernel(const ui
       if (d < p.nbins) {
         const uint32_t c = toff[d];
         toff[d] = run;
+        gdel[d] -= run;  // table offset >= tile offset: counts of the smaller digits of this tile are in both
         run += c;
       }
     }
   }
   __syncthreads();
 
-  // 3. stable local order by digit
+  // 3. stable local order by digit: keys and ids straight to their tile position
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     const uint32_t d = dr[r] >> 16;
     if (d != 0xFFFFu) {
-      const int e = warp * kPerWarp + r * 32 + lane;
-      perm[toff[d] + wpref[warp * nb_pad + d] + (dr[r] & 0xFFFFu)] = static_cast<uint16_t>(e);
+      const uint32_t pos = toff[d] + wpref[warp * nb_pad + d] + (dr[r] & 0xFFFFu);
+      skey[pos] = kk[r];
+      sid[pos] = vv[r];
     }
   }
   __syncthreads();
 
-  // 4. coalesced writes of the digit runs
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const int e = perm[i];
-    const uint32_t key = skey[e];
-    const uint32_t d = digit_of(key, p);
-    const int64_t dest = seg + goff[d] + (static_cast<uint32_t>(i) - toff[d]);
-    keys_out[dest] = key;
-    ids_out[dest] = FIRST ? static_cast<int32_t>(a + e) : sid[e];
+  // 4. coalesced writes of the digit runs (independent iterations, unrolled)
+  constexpr int kPerThread = kTile / (kSortWarps * 32);
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int i = j * kSortWarps * 32 + static_cast<int>(threadIdx.x);
+    if (i < cnt) {
+      const uint32_t key = skey[i];
+      const int64_t dest = seg + gdel[digit_of(key, p)] + static_cast<uint32_t>(i);
+      keys_out[dest] = key;
+      ids_out[dest] = sid[i];
+    }
   }
 }
 
-size_t scatter_smem_bytes(bool first, int nb_pad) {
-  return sizeof(uint32_t) * (kTile + (first ? 0 : kTile) + (2 * kSortWarps + 2) * static_cast<size_t>(nb_pad)) +
-         sizeof(uint16_t) * kTile;
+size_t scatter_smem_bytes(int nb_pad) {
+  return sizeof(uint32_t) * (2 * kTile + (2 * kSortWarps + 2) * static_cast<size_t>(nb_pad));
 }
 
 // Segment starts after a multi-pass partition: seg[t][s] = number of
@@ -280,6 +280,11 @@ __global__ void __launch_bounds__(256) segment_starts_kernel(const uint32_t *ske
   }
 }
 
+__host__ __device__ __forceinline__ uint32_t cpad(uint32_t d) { return d + (d >> 5); }
+__host__ __device__ __forceinline__ uint32_t seg_counter_words(uint32_t lo) {
+  return cpad(1u << lo) + 1u;
+}
+
 struct SegArgs {
   const uint32_t *pkeys;     // [L][n] addresses partitioned by their high bits
   const int32_t *pids;       // [L][n] point ids in the same order
@@ -304,7 +309,9 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
   extern __shared__ uint32_t seg_sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nb = 1u << a.lo, dmask = nb - 1u;
-  uint32_t *cnt = seg_sm + static_cast<size_t>(warp) * nb;
+  // counter of digit d at d + d / 32: a lane's run of 32 consecutive digits
+  // (the scan) and 32 lanes on consecutive digits both touch 32 distinct banks
+  uint32_t *cnt = seg_sm + static_cast<size_t>(warp) * seg_counter_words(a.lo);
   const uint32_t nseg = (1u << a.hb) + 1u;
   const uint64_t total = static_cast<uint64_t>(a.L) * nseg;
   const uint32_t T = 1u << (a.lo + a.hb);
@@ -330,19 +337,19 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
       for (uint32_t i = so + lane; i < se; i += 32) st_l2(out + i, pi[i], keep);
       continue;
     }
-    for (uint32_t d = lane; d < nb; d += 32) cnt[d] = 0;
+    for (uint32_t d = lane; d < nb; d += 32) cnt[cpad(d)] = 0;
     __syncwarp();
     // count the low digits
     {
       uint32_t i = so + lane;
       for (; i + 96 < se; i += 128) {
         const uint32_t k0 = pk[i], k1 = pk[i + 32], k2 = pk[i + 64], k3 = pk[i + 96];
-        atomicAdd(&cnt[k0 & dmask], 1u);
-        atomicAdd(&cnt[k1 & dmask], 1u);
-        atomicAdd(&cnt[k2 & dmask], 1u);
-        atomicAdd(&cnt[k3 & dmask], 1u);
+        atomicAdd(&cnt[cpad(k0 & dmask)], 1u);
+        atomicAdd(&cnt[cpad(k1 & dmask)], 1u);
+        atomicAdd(&cnt[cpad(k2 & dmask)], 1u);
+        atomicAdd(&cnt[cpad(k3 & dmask)], 1u);
       }
-      for (; i < se; i += 32) atomicAdd(&cnt[pk[i] & dmask], 1u);
+      for (; i < se; i += 32) atomicAdd(&cnt[cpad(pk[i] & dmask)], 1u);
     }
     __syncwarp();
     // exclusive scan in place (lane owns a run of consecutive digits); heavy buckets
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
       const uint32_t d0 = min(nb, lane * per), d1 = min(nb, d0 + per);
       uint32_t sum = 0;
       for (uint32_t d = d0; d < d1; ++d) {
-        const uint32_t c = cnt[d];
+        const uint32_t c = cnt[cpad(d)];
         sum += c;
         if (c > a.R && a.heavy_count) {
           const unsigned long long h = atomicAdd(a.heavy_count, 1ULL);
@@ -367,13 +374,13 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
       }
       uint32_t run = so + inc - sum;
       for (uint32_t d = d0; d < d1; ++d) {
-        const uint32_t c = cnt[d];
-        cnt[d] = run;
+        const uint32_t c = cnt[cpad(d)];
+        cnt[cpad(d)] = run;
         run += c;
       }
     }
     __syncwarp();
-    for (uint32_t d = lane; d < nb; d += 32) st_l2(st + ((s << a.lo) | d), cnt[d], keep);
+    for (uint32_t d = lane; d < nb; d += 32) st_l2(st + ((s << a.lo) | d), cnt[cpad(d)], keep);
     __syncwarp();
     // place: rank among equal digits of the round, after the earlier rounds
     for (uint32_t base = so; base < se; base += 128) {
@@ -392,9 +399,9 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
         const bool valid = i < se;
         const uint32_t d = valid ? (kk[r] & dmask) : (nb + static_cast<uint32_t>(lane));
         const uint32_t peers = __match_any_sync(kFull, d);
-        const uint32_t before = valid ? cnt[d] : 0u;
+        const uint32_t before = valid ? cnt[cpad(d)] : 0u;
         __syncwarp();
-        if (valid && (peers & lt_mask) == 0) cnt[d] = before + __popc(peers);
+        if (valid && (peers & lt_mask) == 0) cnt[cpad(d)] = before + __popc(peers);
         __syncwarp();
         if (valid) st_l2(out + before + __popc(peers & lt_mask), id[r], keep);
       }
@@ -443,7 +450,7 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
     radix_hist_kernel<<<grid, 256, 0, stream>>>(kin, s.n, pa, plan.tile, plan.tiles, s.hist);
     radix_scan_kernel<<<s.L, 1024, 0, stream>>>(s.hist, static_cast<int64_t>(pa.nbins) * plan.tiles);
     const int nb_pad = (pa.nbins + 3) & ~3;
-    const size_t smem = scatter_smem_bytes(pass == 0, nb_pad);
+    const size_t smem = scatter_smem_bytes(nb_pad);
     auto kern = pass == 0 ? radix_scatter_kernel<true> : radix_scatter_kernel<false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
       return FLASH_ECUDA;
@@ -486,7 +493,7 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
   if (cudaMemsetAsync(s.claim, 0, sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
   if (s.heavy_count && cudaMemsetAsync(s.heavy_count, 0, sizeof(unsigned long long), stream) != cudaSuccess)
     return FLASH_ECUDA;
-  const size_t smem = sizeof(uint32_t) * kSegWarps * (static_cast<size_t>(1) << plan.lo_bits);
+  const size_t smem = sizeof(uint32_t) * kSegWarps * seg_counter_words(static_cast<uint32_t>(plan.lo_bits));
   if (cudaFuncSetAttribute(segment_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return FLASH_ECUDA;
