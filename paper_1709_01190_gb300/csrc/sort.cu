@@ -13,8 +13,8 @@
 //        hist    : per (table, tile) digit histogram (shared-memory atomics);
 //        scan    : per table exclusive scan of the [digit][tile] counts;
 //        scatter : per (table, tile) stable ranking -- warps take consecutive
-//                  32-element rounds, __match_any_sync ranks equal digits
-//                  within a round, per-warp running counts and a per-digit
+//                  32-element rounds, lanes with equal digits in a round
+//                  find each other through a shared-memory OR mask, per-warp running counts and a per-digit
 //                  prefix over warps keep the tile's element order -- a stable
 //                  local sort of the tile by digit in shared memory, and
 //                  coalesced writes of each digit run to scan offset +
@@ -25,7 +25,8 @@
 //      low digits in shared memory, scans them, writes the bucket starts of
 //      its 2^lo buckets and lists the buckets holding more than R points, and
 //      places every point at its bucket's offset + its rank among the equal
-//      digits before it (32-element rounds in id order, __match_any_sync).
+//      digits before it (32-element rounds in id order, equal digits of a
+//      round found through a shared-memory OR mask).
 //      The segment of sentinels is copied as it is.
 // starts[t][b] = number of addresses < b in table t, for b in [0, 2^rb].
 #include <cuda_runtime.h>
@@ -51,6 +52,16 @@ struct PassArgs {
 
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, const PassArgs &p) {
   return p.top ? (key >> p.shift) : ((key >> p.shift) & ((1u << p.bits) - 1u));
+}
+
+// Lanes of the warp holding the same digit d in this round (valid lanes only):
+// every valid lane ORs its bit into mask[d], and reads the mask back.  The
+// caller clears mask[d] (the round's lowest such lane) after a __syncwarp().
+// A shared-memory OR and a load cost a fraction of __match_any_sync here.
+__device__ __forceinline__ uint32_t round_peers(uint32_t *mask, uint32_t d, bool valid, int lane) {
+  if (valid) atomicOr(&mask[d], 1u << lane);
+  __syncwarp();
+  return valid ? mask[d] : 0u;
 }
 
 __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, int64_t n, PassArgs p, uint32_t tile,
@@ -141,7 +152,11 @@ __global__ void __launch_bounds__(kSortWarps * 32, 3) radix_scatter_kernel(const
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t *my_cnt = wcnt + warp * nb_pad;
   for (int d = threadIdx.x; d < p.nbins; d += blockDim.x) gdel[d] = offs[(static_cast<int64_t>(t) * p.nbins + d) * tiles + ti];
-  for (int d = lane; d < p.nbins; d += 32) my_cnt[d] = 0;
+  uint32_t *my_mask = wpref + warp * nb_pad;  // lanes holding a digit in the current round (step 1 only)
+  for (int d = lane; d < p.nbins; d += 32) {
+    my_cnt[d] = 0;
+    my_mask[d] = 0;
+  }
   __syncwarp();
 
   // 1. load (coalesced) and rank: warp w holds tile elements [w*W, (w+1)*W) in 32-element rounds
@@ -164,11 +179,14 @@ __global__ void __launch_bounds__(kSortWarps * 32, 3) radix_scatter_kernel(const
     const int e = warp * kPerWarp + r * 32 + lane;
     const bool valid = e < cnt;
     const uint32_t d = valid ? digit_of(kk[r], p) : 0xFFFFu;
-    const uint32_t peers = __match_any_sync(kFull, d);
+    const uint32_t peers = round_peers(my_mask, d, valid, lane);
     const uint32_t lower = peers & lt_mask;
     const uint32_t before = valid ? my_cnt[d] : 0u;
     __syncwarp();
-    if (valid && lower == 0) my_cnt[d] = before + __popc(peers);
+    if (valid && lower == 0) {
+      my_cnt[d] = before + __popc(peers);
+      my_mask[d] = 0;
+    }
     __syncwarp();
     dr[r] = (d << 16) | (before + __popc(lower));
   }
@@ -311,7 +329,8 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
   const uint32_t nb = 1u << a.lo, dmask = nb - 1u;
   // counter of digit d at d + d / 32: a lane's run of 32 consecutive digits
   // (the scan) and 32 lanes on consecutive digits both touch 32 distinct banks
-  uint32_t *cnt = seg_sm + static_cast<size_t>(warp) * seg_counter_words(a.lo);
+  uint32_t *cnt = seg_sm + static_cast<size_t>(warp) * (seg_counter_words(a.lo) + nb);
+  uint32_t *msk = cnt + seg_counter_words(a.lo);  // [nb] lanes holding a digit in the current round
   const uint32_t nseg = (1u << a.hb) + 1u;
   const uint64_t total = static_cast<uint64_t>(a.L) * nseg;
   const uint32_t T = 1u << (a.lo + a.hb);
@@ -337,7 +356,10 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
       for (uint32_t i = so + lane; i < se; i += 32) st_l2(out + i, pi[i], keep);
       continue;
     }
-    for (uint32_t d = lane; d < nb; d += 32) cnt[cpad(d)] = 0;
+    for (uint32_t d = lane; d < nb; d += 32) {
+      cnt[cpad(d)] = 0;
+      msk[d] = 0;
+    }
     __syncwarp();
     // count the low digits
     {
@@ -397,11 +419,14 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
         const uint32_t i = base + r * 32 + lane;
         if (base + r * 32 >= se) break;  // warp-uniform
         const bool valid = i < se;
-        const uint32_t d = valid ? (kk[r] & dmask) : (nb + static_cast<uint32_t>(lane));
-        const uint32_t peers = __match_any_sync(kFull, d);
+        const uint32_t d = kk[r] & dmask;
+        const uint32_t peers = round_peers(msk, d, valid, lane);
         const uint32_t before = valid ? cnt[cpad(d)] : 0u;
         __syncwarp();
-        if (valid && (peers & lt_mask) == 0) cnt[cpad(d)] = before + __popc(peers);
+        if (valid && (peers & lt_mask) == 0) {
+          cnt[cpad(d)] = before + __popc(peers);
+          msk[d] = 0;
+        }
         __syncwarp();
         if (valid) st_l2(out + before + __popc(peers & lt_mask), id[r], keep);
       }
@@ -493,7 +518,8 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
   if (cudaMemsetAsync(s.claim, 0, sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
   if (s.heavy_count && cudaMemsetAsync(s.heavy_count, 0, sizeof(unsigned long long), stream) != cudaSuccess)
     return FLASH_ECUDA;
-  const size_t smem = sizeof(uint32_t) * kSegWarps * seg_counter_words(static_cast<uint32_t>(plan.lo_bits));
+  const size_t smem = sizeof(uint32_t) * kSegWarps *
+                      (seg_counter_words(static_cast<uint32_t>(plan.lo_bits)) + (1u << plan.lo_bits));
   if (cudaFuncSetAttribute(segment_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return FLASH_ECUDA;
