@@ -12,10 +12,10 @@
 //       min reduction (even B; odd B takes an element-by-element path that
 //       also marks bins whose minimum is all ones); the bitmap is built
 //       afterwards with ballots;
-//   sparse rows (nnz <= B/2): 32 non-zeros per round; lanes with the same bin
-//       agree on the round's minimum with __match_any_sync /
-//       __reduce_min_sync and one leader per bin updates it, so neither the
-//       bins nor any atomic on them is needed.
+//   sparse rows (nnz <= B/2): 32 non-zeros per round; a bin is set to all
+//       ones when the row first touches it (bitmap bit clear), then every lane
+//       takes a shared-memory min into its bin and sets the bit, so the row
+//       never clears all B bins.
 // Densification (rotation): word by word, lane l takes bin 32w + l; an empty
 // bin j becomes v[src] + (src - j) * 0x9E3779B9, src the first non-empty bin
 // after j, circularly (found from the word bitmap and a ballot summary of the
@@ -154,8 +154,10 @@ __device__ __forceinline__ void emit_empty(const DophParams &a, int64_t r, uint3
   }
 }
 
-// Sparse row (n <= B/2): 32 non-zeros per round; lanes with the same bin
-// agree on the round's minimum and one leader per bin updates it.
+// Sparse row (n <= B/2): 32 non-zeros per round.  A bin is opened at all ones
+// by the lanes that touch it first in the row (its bitmap bit still clear),
+// then every lane takes the min into it and sets the bit; only bins with the
+// bit set are read later, so the row never clears all B bins.
 __device__ __forceinline__ void sparse_row(const DophParams &a, int64_t start, int64_t end, uint32_t *bins,
                                            uint32_t *mask, uint32_t lane) {
   for (uint32_t w = lane; w < a.W; w += 32) mask[w] = 0;
@@ -170,13 +172,11 @@ __device__ __forceinline__ void sparse_row(const DophParams &a, int64_t start, i
     }
     uint32_t bin = 0, off = 0;
     if (valid) bin_and_offset(c, a.s, a.B, bin, off);
-    const uint32_t key = valid ? bin : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(kFull, key);
-    const uint32_t mn = __reduce_min_sync(peers, off);
-    if (valid && (__ffs(peers) - 1) == static_cast<int>(lane)) {
-      const uint32_t bit = 1u << (bin & 31);
-      const uint32_t m = mask[bin >> 5];
-      bins[bin] = (m & bit) ? min(bins[bin], mn) : mn;
+    const uint32_t bit = 1u << (bin & 31);
+    if (valid && !(mask[bin >> 5] & bit)) bins[bin] = 0xFFFFFFFFu;
+    __syncwarp();
+    if (valid) {
+      atomicMin(&bins[bin], off);
       atomicOr(&mask[bin >> 5], bit);
     }
     __syncwarp();

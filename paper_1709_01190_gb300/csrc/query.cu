@@ -640,8 +640,9 @@ __device__ void block_sort_winners(const QArgs &a, uint32_t *sel, uint32_t nsel,
 }
 
 // Radix select of the k-th largest of keys[0..E) (SORTBYVALUE, then the first
-// k), collection and sorted output.  Histogram updates are aggregated per warp
-// (__match_any_sync) because the digits are very skewed (most counts are 1).
+// k), collection and sorted output.  The digits are very skewed (most counts
+// are 1), so the lanes holding lane 0's digit add to its bin once; the others
+// add one by one.
 template <class G>
 __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_t q, const uint32_t *keys,
                              uint32_t E) {
@@ -672,8 +673,14 @@ __device__ void select_phase(const G &g, const QArgs &a, const Region &r, int64_
         const uint32_t i = base + g.rank();
         const uint32_t key = i < E ? keys[i] : 0u;
         const uint32_t d = (i < E && (key & pmask) == prefix) ? ((key >> shift) & 0xFFu) : 0x100u;
-        const uint32_t peers = __match_any_sync(kFull, d);
-        if (d != 0x100u && (peers & lt) == 0) atomicAdd(&r.hist[d], __popc(peers));
+        // lanes sharing lane 0's digit (usually most of them) add once
+        const uint32_t d0 = __shfl_sync(kFull, d, 0);
+        const uint32_t same = __ballot_sync(kFull, d == d0);
+        if (lane == 0) {
+          if (d0 != 0x100u) atomicAdd(&r.hist[d0], __popc(same));
+        } else if (d != d0 && d != 0x100u) {
+          atomicAdd(&r.hist[d], 1u);
+        }
       }
       g.sync();
       if (g.leader_warp()) {
