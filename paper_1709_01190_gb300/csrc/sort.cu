@@ -361,19 +361,27 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
       msk[d] = 0;
     }
     __syncwarp();
-    // count the low digits
+    // count the low digits (the next 128 addresses are loaded while 128 are counted)
     {
-      uint32_t i = so + lane;
-      for (; i + 96 < se; i += 128) {
-        const uint32_t k0 = pk[i], k1 = pk[i + 32], k2 = pk[i + 64], k3 = pk[i + 96];
-        atomicAdd(&cnt[cpad(k0 & dmask)], 1u);
-        atomicAdd(&cnt[cpad(k1 & dmask)], 1u);
-        atomicAdd(&cnt[cpad(k2 & dmask)], 1u);
-        atomicAdd(&cnt[cpad(k3 & dmask)], 1u);
+      uint32_t k[4], kn[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t i = so + r * 32 + lane;
+        k[r] = i < se ? pk[i] : 0xFFFFFFFFu;
       }
-      for (; i < se; i += 32) atomicAdd(&cnt[cpad(pk[i] & dmask)], 1u);
+      for (uint32_t base = so; base < se; base += 128) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const uint32_t i = base + 128 + r * 32 + lane;
+          kn[r] = i < se ? pk[i] : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (k[r] != 0xFFFFFFFFu) atomicAdd(&cnt[cpad(k[r] & dmask)], 1u);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) k[r] = kn[r];
+      }
     }
-    __syncwarp();
     // exclusive scan in place (lane owns a run of consecutive digits); heavy buckets
     {
       const uint32_t per = (nb + 31) / 32;
@@ -405,30 +413,45 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
     for (uint32_t d = lane; d < nb; d += 32) st_l2(st + ((s << a.lo) | d), cnt[cpad(d)], keep);
     __syncwarp();
     // place: rank among equal digits of the round, after the earlier rounds
+    // (the next 128 points are loaded while 128 are placed)
+    uint32_t kk[4];
+    int32_t id[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t i = so + r * 32 + lane;
+      kk[r] = i < se ? pk[i] : 0u;
+      id[r] = i < se ? pi[i] : 0;
+    }
     for (uint32_t base = so; base < se; base += 128) {
-      uint32_t kk[4];
-      int32_t id[4];
+      uint32_t kn[4];
+      int32_t idn[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const uint32_t i = base + r * 32 + lane;
-        kk[r] = i < se ? pk[i] : 0u;
-        id[r] = i < se ? pi[i] : 0;
+        const uint32_t i = base + 128 + r * 32 + lane;
+        kn[r] = i < se ? pk[i] : 0u;
+        idn[r] = i < se ? pi[i] : 0;
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const uint32_t i = base + r * 32 + lane;
-        if (base + r * 32 >= se) break;  // warp-uniform
-        const bool valid = i < se;
-        const uint32_t d = kk[r] & dmask;
-        const uint32_t peers = round_peers(msk, d, valid, lane);
-        const uint32_t before = valid ? cnt[cpad(d)] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt_mask) == 0) {
-          cnt[cpad(d)] = before + __popc(peers);
-          msk[d] = 0;
+        if (base + r * 32 < se) {  // warp-uniform
+          const bool valid = i < se;
+          const uint32_t d = kk[r] & dmask;
+          const uint32_t peers = round_peers(msk, d, valid, lane);
+          const uint32_t before = valid ? cnt[cpad(d)] : 0u;
+          __syncwarp();
+          if (valid && (peers & lt_mask) == 0) {
+            cnt[cpad(d)] = before + __popc(peers);
+            msk[d] = 0;
+          }
+          __syncwarp();
+          if (valid) st_l2(out + before + __popc(peers & lt_mask), id[r], keep);
         }
-        __syncwarp();
-        if (valid) st_l2(out + before + __popc(peers & lt_mask), id[r], keep);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        kk[r] = kn[r];
+        id[r] = idn[r];
       }
     }
   }
