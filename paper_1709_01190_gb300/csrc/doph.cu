@@ -5,13 +5,17 @@
 // One warp hashes one row at a time; rows are handed out dynamically in
 // small groups from a global counter, so very uneven row lengths balance.
 // Per warp, shared memory holds the row's B = K*L bins and a bitmap of the
-// non-empty bins.  Two insertion paths give identical results:
-//   dense rows  (nnz > B/2): bins start at 0xFFFFFFFF; non-zeros are read
-//       as 16-byte vectors, the next 512 of a row prefetched while the
-//       current 512 are hashed, 8 per batch per lane, each by one shared-memory
-//       min reduction (even B; odd B takes an element-by-element path that
-//       also marks bins whose minimum is all ones); the bitmap is built
-//       afterwards with ballots;
+// non-empty bins.  The insertion paths give identical results:
+//   dense rows  (nnz > B/2, B even): bins start at 0xFFFFFFFF; non-zeros are
+//       read as 16-byte vectors, the next 512 of a row prefetched while the
+//       current 512 are hashed, each by one shared-memory min reduction
+//       (off = pi*B mod 2^32 is even, never all ones, so a bin is non-empty
+//       exactly when it is below 0xFFFFFFFF); the columns are range-checked
+//       once per row through a running maximum, and a row holding a column
+//       out of range is redone element by element; rows with every bin
+//       filled skip the bitmap and the densification;
+//   element by element (odd B, or the redo): also marks bins whose minimum is
+//       all ones, and skips (and flags) columns out of range;
 //   sparse rows (nnz <= B/2): 32 non-zeros per round; a bin is set to all
 //       ones when the row first touches it (bitmap bit clear), then every lane
 //       takes a shared-memory min into its bin and sets the bit, so the row
@@ -75,27 +79,35 @@ __device__ __forceinline__ void insert_dense(uint32_t c, const DophParams &a, ui
   }
 }
 
-// Eight non-zeros at once.  `nvalid` (0..8) of them are real; the others are
-// padding.  For an even bin count B, off = pi*B mod 2^32 is even and never
-// 0xFFFFFFFF: every non-zero does an unconditional shared-memory min
-// reduction (padding reduces 0xFFFFFFFF, a no-op), and a bin is non-empty
-// exactly when its value is below 0xFFFFFFFF.  For odd B, or when a column is
-// out of range, the element-by-element path (kept out of line so the hot loop
-// stays small) also records non-zeros whose offset is all ones.
-__device__ __noinline__ void insert8_slow(int4 x, int4 y, int nvalid, const DophParams &a, uint32_t *bins,
-                                          uint32_t *mask) {
-  const uint32_t c[8] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
-                         static_cast<uint32_t>(x.w), static_cast<uint32_t>(y.x), static_cast<uint32_t>(y.y),
-                         static_cast<uint32_t>(y.z), static_cast<uint32_t>(y.w)};
-  for (int i = 0; i < nvalid; ++i) insert_dense(c[i], a, bins, mask);
+// Element-by-element insertion (odd B, or a row holding a column out of
+// range): also records non-zeros whose offset is all ones, and skips (and
+// flags) columns out of range.
+__device__ __noinline__ void insert_row_checked(const DophParams &a, int64_t start, int64_t end, uint32_t *bins,
+                                                uint32_t *mask, uint32_t lane) {
+  for (uint32_t j = lane; j < a.W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
+  for (uint32_t w = lane; w < a.W; w += 32) mask[w] = 0;
+  __syncwarp();
+  for (int64_t e = start + lane; e < end; e += 32) insert_dense(static_cast<uint32_t>(a.col[e]), a, bins, mask);
+  __syncwarp();
 }
 
-// The hash constants come in registers (b1, B, dim): read through `a` they
-// would be reloaded after every reduction (the asm's memory clobber).
+// One non-zero of a dense row (B even, column checked later for the whole
+// row): pi = ((a1_lo*c + b1) >> 32) + a1_hi*c; (bin, off) = (hi, lo) of pi*B.
+// For even B, off = pi*B mod 2^32 is even and never all ones, so a bin is
+// non-empty exactly when its value is below 0xFFFFFFFF.
+__device__ __forceinline__ void insert_fast(uint32_t c, uint32_t a1_lo, uint32_t a1_hi, uint64_t b1, uint32_t B,
+                                            uint32_t *bins) {
+  const uint64_t t = static_cast<uint64_t>(a1_lo) * c + b1;
+  const uint32_t pi = static_cast<uint32_t>(t >> 32) + a1_hi * c;
+  const uint64_t pb = static_cast<uint64_t>(pi) * B;
+  atomicMin(&bins[static_cast<uint32_t>(pb >> 32)], static_cast<uint32_t>(pb));  // result unused: red.shared.min
+}
+
+// Eight non-zeros of a dense row; `nvalid` (0..8) of them are real, the others
+// padding.  mx collects the largest column for the row's range check.
 template <bool MASKED>
-__device__ __forceinline__ void insert8(const int4 &x, const int4 &y, int nvalid, const DophParams &a,
-                                        uint32_t a1_lo, uint32_t a1_hi, uint64_t b1, uint32_t B, uint32_t dim,
-                                        uint32_t bins_s, uint32_t *bins, uint32_t *mask) {
+__device__ __forceinline__ void insert8(const int4 &x, const int4 &y, int nvalid, uint32_t a1_lo, uint32_t a1_hi,
+                                        uint64_t b1, uint32_t B, uint32_t *bins, uint32_t &mx) {
   uint32_t c[8] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
                    static_cast<uint32_t>(x.w), static_cast<uint32_t>(y.x), static_cast<uint32_t>(y.y),
                    static_cast<uint32_t>(y.z), static_cast<uint32_t>(y.w)};
@@ -104,22 +116,11 @@ __device__ __forceinline__ void insert8(const int4 &x, const int4 &y, int nvalid
     for (int i = 0; i < 8; ++i)
       if (i >= nvalid) c[i] = 0;
   }
-  const uint32_t mx = max(max(max(c[0], c[1]), max(c[2], c[3])), max(max(c[4], c[5]), max(c[6], c[7])));
-  if (mx >= dim || (B & 1u)) {
-    insert8_slow(x, y, MASKED ? nvalid : 8, a, bins, mask);
-    return;
-  }
+  mx = __vimax3_u32(mx, __vimax3_u32(c[0], c[1], c[2]), __vimax3_u32(c[3], c[4], c[5]));
+  mx = __vimax3_u32(mx, c[6], c[7]);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    // pi = ((a1_lo*c + b1) >> 32) + a1_hi*c;  (bin, off) = (hi, lo) of pi*B
-    const uint64_t t = static_cast<uint64_t>(a1_lo) * c[i] + b1;
-    const uint32_t pi = static_cast<uint32_t>(t >> 32) + a1_hi * c[i];
-    const uint64_t pb = static_cast<uint64_t>(pi) * B;
-    if (!MASKED || i < nvalid)
-      asm volatile("red.shared.min.u32 [%0], %1;" ::"r"(bins_s + 4u * static_cast<uint32_t>(pb >> 32)),
-                   "r"(static_cast<uint32_t>(pb))
-                   : "memory");
-  }
+  for (int i = 0; i < 8; ++i)
+    if (!MASKED || i < nvalid) insert_fast(c[i], a1_lo, a1_hi, b1, B, bins);
 }
 
 // first set bit index >= from in the summary bitmap (G words), circular over W bits
@@ -196,6 +197,29 @@ __device__ __forceinline__ void dense_mask(const DophParams &a, const uint32_t *
   __syncwarp();
 }
 
+// The emit of row r from its B final bins: the L keys or the B hashes.
+template <bool KEYS>
+__device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const uint32_t *bins, uint32_t lane) {
+  const uint32_t B = a.B;
+  if (KEYS) {
+    const int sh = 64 - static_cast<int>(a.rb);
+    for (uint32_t t = lane; t < a.L; t += 32) {
+      uint64_t x = 0;
+      for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
+      const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
+      if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+      if (a.out_rm) a.out_rm[r * a.L + t] = key;
+    }
+  } else if (a.vec_out) {
+    uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
+    const uint4 *src = reinterpret_cast<const uint4 *>(bins);
+    for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
+  } else {
+    for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
+  }
+  __syncwarp();
+}
+
 // Densification by rotation and the emit of row r (keys or hashes).
 template <bool KEYS>
 __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint32_t *bins, const uint32_t *mask,
@@ -237,23 +261,7 @@ __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint3
     }
     __syncwarp();
   }
-  if (KEYS) {
-    const int sh = 64 - static_cast<int>(a.rb);
-    for (uint32_t t = lane; t < a.L; t += 32) {
-      uint64_t x = 0;
-      for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
-      const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
-      if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
-      if (a.out_rm) a.out_rm[r * a.L + t] = key;
-    }
-  } else if (a.vec_out) {
-    uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
-    const uint4 *src = reinterpret_cast<const uint4 *>(bins);
-    for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
-  } else {
-    for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
-  }
-  __syncwarp();
+  emit_row<KEYS>(a, r, bins, lane);
 }
 
 // The 16-byte aligned body [a4, a4 + 4 nq) of the row [start, end), from the
@@ -278,7 +286,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
   const uint32_t a1_lo = static_cast<uint32_t>(a.s.a1), a1_hi = static_cast<uint32_t>(a.s.a1 >> 32);
   const uint64_t b1 = a.s.b1;
   const uint32_t dim = a.dim_u32;
-  const uint32_t bins_s = static_cast<uint32_t>(__cvta_generic_to_shared(bins));
   const int4 zero = make_int4(0, 0, 0, 0);
   const int64_t G = a.rows_per_grab;
   const int64_t mis = static_cast<int64_t>((reinterpret_cast<uintptr_t>(a.col) >> 2) & 3u);
@@ -312,19 +319,38 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
 
     if (n <= static_cast<int64_t>(B / 2)) {
       sparse_row(a, start, end, bins, mask, lane);
+      finish_row<KEYS>(a, r, bins, mask, lane);
+    } else if (B & 1u) {  // odd B: element by element
+      insert_row_checked(a, start, end, bins, mask, lane);
+      dense_mask(a, bins, mask, lane);
+      finish_row<KEYS>(a, r, bins, mask, lane);
     } else {
       // ---- dense row: head up to a 16-byte boundary, 16-byte body in groups
-      // of 128 int4 (4 per lane), the last group partial, tail
-      for (uint32_t j = lane; j < W * 32; j += 32) bins[j] = 0xFFFFFFFFu;
-      for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
+      // of 128 int4 (4 per lane), the last group partial, tail; the columns
+      // are range-checked once per row (a row holding one out of range is
+      // redone element by element)
+      {
+        uint4 *b4 = reinterpret_cast<uint4 *>(bins);
+        const uint4 ones = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        for (uint32_t q4 = lane; q4 < W * 8; q4 += 32) b4[q4] = ones;
+      }
       __syncwarp();
       int64_t a4, nq;
       row_body(start, end, mis, a4, nq);
       const int64_t b4 = a4 + 4 * nq;
       const int4 *body = reinterpret_cast<const int4 *>(a.col + a4);
       const int64_t nfull = nq >> 7;
-      if (start + static_cast<int64_t>(lane) < a4) insert_dense(static_cast<uint32_t>(a.col[start + lane]), a, bins, mask);
-      if (b4 + static_cast<int64_t>(lane) < end) insert_dense(static_cast<uint32_t>(a.col[b4 + lane]), a, bins, mask);
+      uint32_t mx = 0;
+      if (start + static_cast<int64_t>(lane) < a4) {
+        const uint32_t c = static_cast<uint32_t>(a.col[start + lane]);
+        mx = max(mx, c);
+        insert_fast(c, a1_lo, a1_hi, b1, B, bins);
+      }
+      if (b4 + static_cast<int64_t>(lane) < end) {
+        const uint32_t c = static_cast<uint32_t>(a.col[b4 + lane]);
+        mx = max(mx, c);
+        insert_fast(c, a1_lo, a1_hi, b1, B, bins);
+      }
       int4 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
       if (nfull > 0) {
         const int4 *p0 = body + lane;
@@ -342,8 +368,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
           n2 = __ldcs(pn + 64);
           n3 = __ldcs(pn + 96);
         }
-        insert8<false>(g0, g1, 8, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
-        insert8<false>(g2, g3, 8, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
+        insert8<false>(g0, g1, 8, a1_lo, a1_hi, b1, B, bins, mx);
+        insert8<false>(g2, g3, 8, a1_lo, a1_hi, b1, B, bins, mx);
         g0 = n0;
         g1 = n1;
         g2 = n2;
@@ -358,12 +384,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
         g3 = q0 + 96 < nq ? __ldcs(body + q0 + 96) : zero;
         const int v01 = (q0 < nq ? 4 : 0) + (q0 + 32 < nq ? 4 : 0);
         const int v23 = (q0 + 64 < nq ? 4 : 0) + (q0 + 96 < nq ? 4 : 0);
-        insert8<true>(g0, g1, v01, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
-        insert8<true>(g2, g3, v23, a, a1_lo, a1_hi, b1, B, dim, bins_s, bins, mask);
+        insert8<true>(g0, g1, v01, a1_lo, a1_hi, b1, B, bins, mx);
+        insert8<true>(g2, g3, v23, a1_lo, a1_hi, b1, B, bins, mx);
       }
-      dense_mask(a, bins, mask, lane);
+      __syncwarp();
+      const bool bad = __any_sync(kFull, mx >= dim);
+      if (bad) insert_row_checked(a, start, end, bins, mask, lane);
+      // rows with every bin filled (nearly all dense rows) skip the bitmap and densification
+      bool empty_bin = false;
+      for (uint32_t j = lane; j < B; j += 32) empty_bin |= bins[j] == 0xFFFFFFFFu;
+      if (__any_sync(kFull, empty_bin)) {
+        for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
+        dense_mask(a, bins, mask, lane);
+        finish_row<KEYS>(a, r, bins, mask, lane);
+      } else {
+        emit_row<KEYS>(a, r, bins, lane);
+      }
     }
-    finish_row<KEYS>(a, r, bins, mask, lane);
   }
 }
 
