@@ -103,24 +103,27 @@ __device__ __forceinline__ void insert_fast(uint32_t c, uint32_t a1_lo, uint32_t
   atomicMin(&bins[static_cast<uint32_t>(pb >> 32)], static_cast<uint32_t>(pb));  // result unused: red.shared.min
 }
 
-// Eight non-zeros of a dense row; `nvalid` (0..8) of them are real, the others
-// padding.  mx collects the largest column for the row's range check.
-template <bool MASKED>
-__device__ __forceinline__ void insert8(const int4 &x, const int4 &y, int nvalid, uint32_t a1_lo, uint32_t a1_hi,
-                                        uint64_t b1, uint32_t B, uint32_t *bins, uint32_t &mx) {
-  uint32_t c[8] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
-                   static_cast<uint32_t>(x.w), static_cast<uint32_t>(y.x), static_cast<uint32_t>(y.y),
-                   static_cast<uint32_t>(y.z), static_cast<uint32_t>(y.w)};
-  if (MASKED) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (i >= nvalid) c[i] = 0;
-  }
+// Eight non-zeros of a dense row; mx collects the largest column for the
+// row's range check.
+__device__ __forceinline__ void insert8(const int4 &x, const int4 &y, uint32_t a1_lo, uint32_t a1_hi, uint64_t b1,
+                                        uint32_t B, uint32_t *bins, uint32_t &mx) {
+  const uint32_t c[8] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
+                         static_cast<uint32_t>(x.w), static_cast<uint32_t>(y.x), static_cast<uint32_t>(y.y),
+                         static_cast<uint32_t>(y.z), static_cast<uint32_t>(y.w)};
   mx = __vimax3_u32(mx, __vimax3_u32(c[0], c[1], c[2]), __vimax3_u32(c[3], c[4], c[5]));
   mx = __vimax3_u32(mx, c[6], c[7]);
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-    if (!MASKED || i < nvalid) insert_fast(c[i], a1_lo, a1_hi, b1, B, bins);
+  for (int i = 0; i < 8; ++i) insert_fast(c[i], a1_lo, a1_hi, b1, B, bins);
+}
+
+// Four non-zeros (the partial last group, one 16-byte part at a time).
+__device__ __forceinline__ void insert4(const int4 &x, uint32_t a1_lo, uint32_t a1_hi, uint64_t b1, uint32_t B,
+                                        uint32_t *bins, uint32_t &mx) {
+  const uint32_t c[4] = {static_cast<uint32_t>(x.x), static_cast<uint32_t>(x.y), static_cast<uint32_t>(x.z),
+                         static_cast<uint32_t>(x.w)};
+  mx = __vimax3_u32(mx, __vimax3_u32(c[0], c[1], c[2]), c[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) insert_fast(c[i], a1_lo, a1_hi, b1, B, bins);
 }
 
 // first set bit index >= from in the summary bitmap (G words), circular over W bits
@@ -368,24 +371,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
           n2 = __ldcs(pn + 64);
           n3 = __ldcs(pn + 96);
         }
-        insert8<false>(g0, g1, 8, a1_lo, a1_hi, b1, B, bins, mx);
-        insert8<false>(g2, g3, 8, a1_lo, a1_hi, b1, B, bins, mx);
+        insert8(g0, g1, a1_lo, a1_hi, b1, B, bins, mx);
+        insert8(g2, g3, a1_lo, a1_hi, b1, B, bins, mx);
         g0 = n0;
         g1 = n1;
         g2 = n2;
         g3 = n3;
       }
       if ((nfull << 7) < nq) {
-        // the valid slots of a lane are a prefix: each batch has 0, 4 or 8 real non-zeros
+        // the valid 16-byte parts of a lane are a prefix
         const int64_t q0 = (nfull << 7) + lane;
         g0 = q0 < nq ? __ldcs(body + q0) : zero;
         g1 = q0 + 32 < nq ? __ldcs(body + q0 + 32) : zero;
         g2 = q0 + 64 < nq ? __ldcs(body + q0 + 64) : zero;
         g3 = q0 + 96 < nq ? __ldcs(body + q0 + 96) : zero;
-        const int v01 = (q0 < nq ? 4 : 0) + (q0 + 32 < nq ? 4 : 0);
-        const int v23 = (q0 + 64 < nq ? 4 : 0) + (q0 + 96 < nq ? 4 : 0);
-        insert8<true>(g0, g1, v01, a1_lo, a1_hi, b1, B, bins, mx);
-        insert8<true>(g2, g3, v23, a1_lo, a1_hi, b1, B, bins, mx);
+        if (q0 < nq) insert4(g0, a1_lo, a1_hi, b1, B, bins, mx);
+        if (q0 + 32 < nq) insert4(g1, a1_lo, a1_hi, b1, B, bins, mx);
+        if (q0 + 64 < nq) insert4(g2, a1_lo, a1_hi, b1, B, bins, mx);
+        if (q0 + 96 < nq) insert4(g3, a1_lo, a1_hi, b1, B, bins, mx);
       }
       __syncwarp();
       const bool bad = __any_sync(kFull, mx >= dim);
