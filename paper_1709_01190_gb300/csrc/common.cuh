@@ -77,24 +77,27 @@ __device__ __forceinline__ uint32_t reservoir_draw(uint64_t bucket_key, uint32_t
 // Per-access hints (no device setting changes): data that a later phase reads
 // at random (bucket starts, grouped ids) is kept with evict_last; streams read
 // or written once go with evict_first.
+// The policies and the loads are pure (no volatile): the compiler may hoist,
+// share and schedule them like ordinary loads of data that no kernel writes
+// while it runs.
 __device__ __forceinline__ uint64_t l2_policy_keep() {
   uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ uint64_t l2_policy_stream() {
   uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ uint32_t ld_l2(const uint32_t *ptr, uint64_t pol) {
   uint32_t v;
-  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
   return v;
 }
 __device__ __forceinline__ int32_t ld_l2(const int32_t *ptr, uint64_t pol) {
   int32_t v;
-  asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
   return v;
 }
 __device__ __forceinline__ void st_l2(uint32_t *ptr, uint32_t v, uint64_t pol) {
