@@ -100,11 +100,13 @@ __device__ __forceinline__ int32_t ld_l2(const int32_t *ptr, uint64_t pol) {
   asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
   return v;
 }
+// Stores of results the writing kernel never reads back: no memory clobber,
+// so loads and shared-memory work around them stay schedulable.
 __device__ __forceinline__ void st_l2(uint32_t *ptr, uint32_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol));
 }
 __device__ __forceinline__ void st_l2(int32_t *ptr, int32_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+  asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol));
 }
 
 inline unsigned div_up(uint64_t a, uint64_t b) { return static_cast<unsigned>((a + b - 1) / b); }
