@@ -168,6 +168,8 @@ def test_keys_adversarial():
     assert np.array_equal(got, exp)
 
 
+# The sort partitions each table by the address bits above the low 10, in
+# passes of at most 8 bits, then sorts every segment of 2^10 buckets by one warp.
 BUILD_CASES = [
     ("tiny_plain", 10_000, None),
     ("tiny_plain", 3_001, dict(range_bits=6, R=3)),       # many heavy buckets
@@ -175,9 +177,13 @@ BUILD_CASES = [
     ("tiny_plain", 4_000, dict(range_bits=9, R=200, L=4)),  # R above every occupancy
     ("url_like_batched", 30_000, dict(range_bits=12)),   # Zipf heavy buckets, R = 128
     ("kdd12_like", 40_000, dict(range_bits=13, L=32)),
-    ("kdd12_like", 30_000, dict(range_bits=20, L=4, R=2)),          # two 10-bit digit passes
-    ("url_like_batched", 20_000, dict(range_bits=21, L=2, R=4, K=2)),  # three passes
-    ("tiny_plain", 5_000, dict(range_bits=10, R=4)),                 # one pass
+    ("kdd12_like", 30_000, dict(range_bits=20, L=4, R=2)),          # 10 high bits: two passes
+    ("url_like_batched", 20_000, dict(range_bits=21, L=2, R=4, K=2)),  # 11 high bits: two passes
+    ("url_like_batched", 20_000, dict(range_bits=19, L=2, R=4)),    # 9 high bits: two passes
+    ("tiny_plain", 20_000, dict(range_bits=24, L=1, R=2)),          # 14 high bits, segments mostly empty
+    ("webspam_like", 5_000, dict(range_bits=18, L=8)),              # 8 high bits: one pass
+    ("tiny_plain", 5_000, dict(range_bits=10, R=4)),                # no high bits: one segment per table
+    ("tiny_plain", 100_000, dict(range_bits=10, L=2, R=8)),         # one warp places 100,000 points
     ("tiny_plain", 5_000, dict(range_bits=1, R=64, L=3)),            # two buckets: m >> R everywhere
 ]
 
