@@ -48,15 +48,15 @@ def _lib():
     if _LIB is None:
         lib = ctypes.CDLL(build())
         lib.oracle_seeds.argtypes = [_U64, _P]
-        lib.oracle_hash.argtypes = [_P, _P, _I64, _I64, _U32, _U32, _U64, _P]
-        lib.oracle_keys.argtypes = [_P, _P, _I64, _I64, _U32, _U32, _U32, _U64, _P, _I64]
-        lib.oracle_build.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _P, _P]
+        lib.oracle_hash.argtypes = [_P, _P, _I64, _I64, _U32, _U32, _U64, _U32, _P]
+        lib.oracle_keys.argtypes = [_P, _P, _I64, _I64, _U32, _U32, _U32, _U64, _U32, _P, _I64]
+        lib.oracle_build.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _U32, _P, _P]
         lib.oracle_bucket.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U64, _P, _P]
         lib.oracle_kselect.argtypes = [_P, _I64, _I32, _I32, _P, _P]
-        lib.oracle_query.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _U64, _P, _P, _I64, _I32, _P, _P, _P]
+        lib.oracle_query.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _U64, _U32, _P, _P, _I64, _I32, _P, _P, _P]
         lib.oracle_query_one_streamed.argtypes = [_P, _I64, _P, _I64, _U32, _U32, _U64, _P, ctypes.c_int,
                                                   _I32, _I32, _P, _P]
-        lib.oracle_knn_graph.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _I32, _P, _P]
+        lib.oracle_knn_graph.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _U32, _I32, _P, _P]
         lib.oracle_address.argtypes = [_P, _U32, _U32, _U32, _U32, _U64]
         lib.oracle_build_tables_from_keys.argtypes = [_P, _I64, _P, _I64, _U32, _U32, _U32, _U32, _U64, _P, _P]
         lib.oracle_address.restype = ctypes.c_uint32
@@ -92,8 +92,8 @@ def seeds(seed: int) -> dict:
     return dict(zip(("a1", "b1", "a2", "b2", "r"), (int(x) for x in out)))
 
 
-def doph(row_ptr, col, K: int, L: int, seed: int, rows=None, n_threads=None) -> np.ndarray:
-    """DOPH hashes, uint32 [n_rows][K*L] (Section 2.3 on Eq. 1)."""
+def doph(row_ptr, col, K: int, L: int, seed: int, rows=None, n_threads=None, densify: int = 0) -> np.ndarray:
+    """DOPH hashes, uint32 [n_rows][K*L] (Section 2.3 on Eq. 1); densify 0 = rotation, 1 = optimal."""
     rp, prp = _c(row_ptr, np.int64)
     cl, pcl = _c(col, np.int32)
     n = rp.shape[0] - 1
@@ -102,7 +102,7 @@ def doph(row_ptr, col, K: int, L: int, seed: int, rows=None, n_threads=None) -> 
         rows = np.asarray(rows, dtype=np.int64)
         out = np.empty((len(rows), B), dtype=np.uint32)
         for i, r in enumerate(rows):
-            _check(_lib().oracle_hash(prp, pcl, int(r), int(r) + 1, K, L, seed, out[i].ctypes.data))
+            _check(_lib().oracle_hash(prp, pcl, int(r), int(r) + 1, K, L, seed, densify, out[i].ctypes.data))
         return out
     out = np.empty((n, B), dtype=np.uint32)
     chunks = _chunks(n, _workers(n_threads))
@@ -110,13 +110,13 @@ def doph(row_ptr, col, K: int, L: int, seed: int, rows=None, n_threads=None) -> 
 
     def run(ab):
         a, b = ab
-        _check(lib.oracle_hash(prp, pcl, a, b, K, L, seed, out[a:b].ctypes.data if b > a else None))
+        _check(lib.oracle_hash(prp, pcl, a, b, K, L, seed, densify, out[a:b].ctypes.data if b > a else None))
 
     _pmap(run, chunks)
     return out
 
 
-def keys(row_ptr, col, K: int, L: int, range_bits: int, seed: int, n_threads=None) -> np.ndarray:
+def keys(row_ptr, col, K: int, L: int, range_bits: int, seed: int, n_threads=None, densify: int = 0) -> np.ndarray:
     """Table addresses, uint32 [L][n_rows] (MapKHashesToAddress per table)."""
     rp, prp = _c(row_ptr, np.int64)
     cl, pcl = _c(col, np.int32)
@@ -127,7 +127,7 @@ def keys(row_ptr, col, K: int, L: int, range_bits: int, seed: int, n_threads=Non
     def run(ab):
         a, b = ab
         if b > a:
-            _check(lib.oracle_keys(prp, pcl, a, b, K, L, range_bits, seed, out[:, a:].ctypes.data, n))
+            _check(lib.oracle_keys(prp, pcl, a, b, K, L, range_bits, seed, densify, out[:, a:].ctypes.data, n))
 
     _pmap(run, _chunks(n, _workers(n_threads)))
     return out
@@ -140,7 +140,7 @@ def address(h, t: int, K: int, L: int, range_bits: int, seed: int) -> int:
     return int(_lib().oracle_address(ph, t, K, L, range_bits, seed))
 
 
-def build_tables(row_ptr, col, K, L, R, range_bits, seed):
+def build_tables(row_ptr, col, K, L, R, range_bits, seed, densify=0):
     """Adding phase (Algorithm 2).  Returns (tables int32 [L][2^rb][R], counts uint32 [L][2^rb])."""
     rp, prp = _c(row_ptr, np.int64)
     cl, pcl = _c(col, np.int32)
@@ -148,7 +148,8 @@ def build_tables(row_ptr, col, K, L, R, range_bits, seed):
     T = 1 << range_bits
     tables = np.empty((L, T, R), dtype=np.int32)
     counts = np.empty((L, T), dtype=np.uint32)
-    _check(_lib().oracle_build(prp, pcl, n, K, L, R, range_bits, seed, tables.ctypes.data, counts.ctypes.data))
+    _check(_lib().oracle_build(prp, pcl, n, K, L, R, range_bits, seed, densify, tables.ctypes.data,
+                               counts.ctypes.data))
     return tables, counts
 
 
@@ -172,7 +173,7 @@ def kselect(A, k: int, exclude: int = -1):
     return ids, cnt
 
 
-def query(tables, counts, K, L, R, range_bits, seed, q_row_ptr, q_col, k, exclude=None):
+def query(tables, counts, K, L, R, range_bits, seed, q_row_ptr, q_col, k, exclude=None, densify=0):
     """Querying phase (Algorithm 3).  Returns (ids int32 [nq][k], counts int32 [nq][k])."""
     tb, ptb = _c(tables, np.int32)
     ct, pct = _c(counts, np.uint32)
@@ -184,7 +185,7 @@ def query(tables, counts, K, L, R, range_bits, seed, q_row_ptr, q_col, k, exclud
     ex = None
     if exclude is not None:
         ex, pex = _c(exclude, np.int32)
-    _check(_lib().oracle_query(ptb, pct, K, L, R, range_bits, seed, prp, pcl if cl.size else None, nq, k,
+    _check(_lib().oracle_query(ptb, pct, K, L, R, range_bits, seed, densify, prp, pcl if cl.size else None, nq, k,
                                None if ex is None else pex, ids.ctypes.data, cnt.ctypes.data))
     return ids, cnt
 
@@ -201,26 +202,26 @@ def query_streamed(keys_all, row_ptr, L, R, seed, q_keys, q_empty, k, exclude=-1
     return ids, cnt
 
 
-def knn_graph(row_ptr, col, K, L, R, range_bits, seed, k):
+def knn_graph(row_ptr, col, K, L, R, range_bits, seed, k, densify=0):
     """All-points k-NN graph: build on all rows, query every row excluding itself."""
     rp, prp = _c(row_ptr, np.int64)
     cl, pcl = _c(col, np.int32)
     n = rp.shape[0] - 1
     ids = np.empty((n, k), dtype=np.int32)
     cnt = np.empty((n, k), dtype=np.int32)
-    _check(_lib().oracle_knn_graph(prp, pcl if cl.size else None, n, K, L, R, range_bits, seed, k,
+    _check(_lib().oracle_knn_graph(prp, pcl if cl.size else None, n, K, L, R, range_bits, seed, densify, k,
                                    ids.ctypes.data, cnt.ctypes.data))
     return ids, cnt
 
 
-def build_tables_threaded(row_ptr, col, K, L, R, range_bits, seed, n_threads=None):
+def build_tables_threaded(row_ptr, col, K, L, R, range_bits, seed, n_threads=None, densify=0):
     """build_tables with the addresses computed on several threads (row blocks) and the tables
     built on several threads (each table is an independent Adding phase, Section 3.4); the
     result equals build_tables."""
     rp, prp = _c(row_ptr, np.int64)
     n = rp.shape[0] - 1
     T = 1 << range_bits
-    ks = keys(row_ptr, col, K, L, range_bits, seed, n_threads)
+    ks = keys(row_ptr, col, K, L, range_bits, seed, n_threads, densify)
     tables = np.empty((L, T, R), dtype=np.int32)
     counts = np.empty((L, T), dtype=np.uint32)
     lib = _lib()
@@ -233,13 +234,13 @@ def build_tables_threaded(row_ptr, col, K, L, R, range_bits, seed, n_threads=Non
     return tables, counts
 
 
-def knn_graph_threaded(row_ptr, col, K, L, R, range_bits, seed, k, n_threads=None):
+def knn_graph_threaded(row_ptr, col, K, L, R, range_bits, seed, k, n_threads=None, densify=0):
     """knn_graph on several threads: build_tables_threaded, then the queries in row blocks; the
     result equals knn_graph."""
     rp, _ = _c(row_ptr, np.int64)
     cl, _ = _c(col, np.int32)
     n = rp.shape[0] - 1
-    tables, counts = build_tables_threaded(rp, cl, K, L, R, range_bits, seed, n_threads)
+    tables, counts = build_tables_threaded(rp, cl, K, L, R, range_bits, seed, n_threads, densify)
     ids = np.empty((n, k), dtype=np.int32)
     cnt = np.empty((n, k), dtype=np.int32)
 
@@ -248,7 +249,7 @@ def knn_graph_threaded(row_ptr, col, K, L, R, range_bits, seed, k, n_threads=Non
         if b > a:
             sub_rp = rp[a:b + 1] - rp[a]
             i, c = query(tables, counts, K, L, R, range_bits, seed, sub_rp, cl[rp[a]:rp[b]], k,
-                         exclude=np.arange(a, b, dtype=np.int32))
+                         exclude=np.arange(a, b, dtype=np.int32), densify=densify)
             ids[a:b] = i
             cnt[a:b] = c
 

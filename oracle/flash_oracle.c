@@ -14,8 +14,10 @@
  *   - the Adding phase with reservoir sampling, Algorithms 1 and 2;
  *   - the Querying phase with count-based k-selection, Algorithm 3.
  * Where the paper leaves a choice open (the hash family, densification
- * variant, which K hashes form table t, the random-number generator) the
- * fixed reading is stated at the function that uses it.
+ * variant -- rotation, or the optimal densification of [36] the paper cites,
+ * chosen by a densify argument --, which K hashes form table t, the
+ * random-number generator) the fixed reading is stated at the function that
+ * uses it.
  *
  * All arithmetic is on unsigned integers with wrap-around modulo 2^w.
  */
@@ -26,12 +28,14 @@
 /* ------------------------------------------------------------------ seeds
  * Section 2.3: DOPH needs only a handful of random numbers.  Reading: the
  * user seed s starts a SplitMix64 sequence (Steele, Lea & Flood, OOPSLA
- * 2014); its first five outputs are a1, b1, a2, b2, r with a1, a2 forced odd.
+ * 2014); its first six outputs are a1, b1, a2, b2, r, d with a1, a2 forced
+ * odd.
  *   a1, b1 : the permutation surrogate pi (one-permutation hashing)
  *   a2, b2 : MapKHashesToAddress
- *   r      : key of the reservoir random numbers (Algorithm 1 / 2)          */
+ *   r      : key of the reservoir random numbers (Algorithm 1 / 2)
+ *   d      : key of the probe sequence of optimal densification            */
 typedef struct {
-  uint64_t a1, b1, a2, b2, r;
+  uint64_t a1, b1, a2, b2, r, d;
 } oracle_seeds_t;
 
 static uint64_t splitmix64_next(uint64_t *state) {
@@ -58,6 +62,7 @@ static oracle_seeds_t make_seeds(uint64_t seed) {
   s.a2 = splitmix64_next(&st) | 1ULL;
   s.b2 = splitmix64_next(&st);
   s.r = splitmix64_next(&st);
+  s.d = splitmix64_next(&st);
   return s;
 }
 
@@ -80,13 +85,21 @@ void oracle_seeds(uint64_t seed, uint64_t out[5]) {
  * bin off increases with pi, so "smallest off" is "smallest pi" (Eq. 1).
  *
  * OPH: v[j] = min{ off(i) : x_i != 0, bin(i) = j }, empty if no such i.
- * Densification (reading: rotation, Shrivastava & Li, UAI 2014): an empty
- * bin j takes the value of the first non-empty bin to its right,
- * circularly, at distance t >= 1, plus t * 0x9E3779B9 (mod 2^32).
+ * Two densifications of the empty bins (densify = 0 or 1):
+ *  0, rotation (Shrivastava & Li, UAI 2014): an empty bin j takes the value
+ *     of the first non-empty bin to its right, circularly, at distance
+ *     t >= 1, plus t * 0x9E3779B9 (mod 2^32);
+ *  1, optimal densification (the variant Section 2.3 cites as [36]; the
+ *     paper does not define it, reading): an empty bin j probes the bins
+ *         src_i = ((mix(d XOR (j * 2^32 + i)) >> 32) * B) >> 32,
+ *     mix = the SplitMix64 output function (a random hash of (bin,
+ *     attempt)), for attempts i = 1, 2, ..., 8B, and copies the value of the
+ *     first non-empty one, unchanged; if all 8B probes are empty it copies
+ *     the first non-empty bin to its right, circularly, unchanged.
  * An empty row (no non-zeros) hashes to 0xFFFFFFFF in every bin.
  * Values x_i are ignored: the hash sees only the set of non-zero columns.   */
-static void doph_row(const int32_t *cols, int64_t nnz, uint32_t B, const oracle_seeds_t *s, uint32_t *h,
-                     uint32_t *v, uint8_t *filled, uint32_t *next_src) {
+static void doph_row(const int32_t *cols, int64_t nnz, uint32_t B, const oracle_seeds_t *s, uint32_t densify,
+                     uint32_t *h, uint32_t *v, uint8_t *filled, uint32_t *next_src) {
   int64_t e;
   uint32_t j;
   if (nnz == 0) {
@@ -121,8 +134,20 @@ static void doph_row(const int32_t *cols, int64_t nnz, uint32_t B, const oracle_
   }
   for (j = 0; j < B; ++j) {
     uint32_t src = next_src[j];
-    uint32_t t = src >= j ? src - j : src + B - j;
-    h[j] = v[src] + t * 0x9E3779B9u;
+    if (densify == 0) {
+      uint32_t t = src >= j ? src - j : src + B - j;
+      h[j] = v[src] + t * 0x9E3779B9u;
+    } else if (filled[j]) {
+      h[j] = v[j];
+    } else {
+      uint64_t i;
+      for (i = 1; i <= 8ULL * B; ++i) {
+        uint64_t u = splitmix64_mix(s->d ^ (((uint64_t)j << 32) | i));
+        uint32_t probe = (uint32_t)(((u >> 32) * (uint64_t)B) >> 32);
+        if (filled[probe]) { src = probe; break; }
+      }
+      h[j] = v[src];
+    }
   }
 }
 
@@ -172,7 +197,7 @@ static void add(int32_t *reservoir, uint32_t *counter, uint32_t R, uint64_t r, u
 
 /* hashes of rows [r0, r1) -> out[(r - r0) * B + j], B = K*L               */
 int oracle_hash(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t r1, uint32_t K, uint32_t L,
-                uint64_t seed, uint32_t *out) {
+                uint64_t seed, uint32_t densify, uint32_t *out) {
   uint32_t B = K * L;
   oracle_seeds_t s = make_seeds(seed);
   uint32_t *v = (uint32_t *)malloc(sizeof(uint32_t) * B);
@@ -181,7 +206,8 @@ int oracle_hash(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t 
   int64_t r;
   if (!v || !filled || !nx) { free(v); free(filled); free(nx); return -1; }
   for (r = r0; r < r1; ++r)
-    doph_row(col + row_ptr[r], row_ptr[r + 1] - row_ptr[r], B, &s, out + (r - r0) * (int64_t)B, v, filled, nx);
+    doph_row(col + row_ptr[r], row_ptr[r + 1] - row_ptr[r], B, &s, densify, out + (r - r0) * (int64_t)B, v, filled,
+             nx);
   free(v);
   free(filled);
   free(nx);
@@ -190,7 +216,7 @@ int oracle_hash(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t 
 
 /* table addresses of rows [r0, r1) -> keys[t * ld + (r - r0)]              */
 int oracle_keys(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t r1, uint32_t K, uint32_t L,
-                uint32_t rb, uint64_t seed, uint32_t *keys, int64_t ld) {
+                uint32_t rb, uint64_t seed, uint32_t densify, uint32_t *keys, int64_t ld) {
   uint32_t B = K * L, t;
   oracle_seeds_t s = make_seeds(seed);
   uint32_t *h = (uint32_t *)malloc(sizeof(uint32_t) * B);
@@ -200,7 +226,7 @@ int oracle_keys(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t 
   int64_t r;
   if (!h || !v || !filled || !nx) { free(h); free(v); free(filled); free(nx); return -1; }
   for (r = r0; r < r1; ++r) {
-    doph_row(col + row_ptr[r], row_ptr[r + 1] - row_ptr[r], B, &s, h, v, filled, nx);
+    doph_row(col + row_ptr[r], row_ptr[r + 1] - row_ptr[r], B, &s, densify, h, v, filled, nx);
     for (t = 0; t < L; ++t) keys[(int64_t)t * ld + (r - r0)] = map_k_hashes_to_address(h, t, K, L, rb, &s);
   }
   free(h);
@@ -216,7 +242,7 @@ int oracle_keys(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t 
  * counts[t * 2^rb + key] = number of arrivals (not capped at R).
  * Reading: a row with no non-zeros is not inserted anywhere.              */
 int oracle_build(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t K, uint32_t L, uint32_t R,
-                 uint32_t rb, uint64_t seed, int32_t *tables, uint32_t *counts) {
+                 uint32_t rb, uint64_t seed, uint32_t densify, int32_t *tables, uint32_t *counts) {
   uint32_t B = K * L, t;
   uint64_t T = 1ULL << rb;
   oracle_seeds_t s = make_seeds(seed);
@@ -232,7 +258,7 @@ int oracle_build(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t
   for (p = 0; p < n; ++p) {                                   /* for each DataPoint */
     int64_t nnz = row_ptr[p + 1] - row_ptr[p];
     if (nnz == 0) continue;
-    doph_row(col + row_ptr[p], nnz, B, &s, all_hashes, v, filled, nx);   /* AllHashes := DOPH */
+    doph_row(col + row_ptr[p], nnz, B, &s, densify, all_hashes, v, filled, nx);   /* AllHashes := DOPH */
     for (t = 0; t < L; ++t) {                                 /* for each Table_t */
       uint32_t key = map_k_hashes_to_address(all_hashes, t, K, L, rb, &s);
       uint64_t bucket = (uint64_t)t * T + key;
@@ -349,7 +375,7 @@ int oracle_kselect(int32_t *A, int64_t n, int32_t exclude, int32_t k, int32_t *o
  * out := KSELECT(A).  exclude may be NULL (no exclusion).
  * Reading: a query row with no non-zeros reports nothing.                 */
 int oracle_query(const int32_t *tables, const uint32_t *counts, uint32_t K, uint32_t L, uint32_t R, uint32_t rb,
-                 uint64_t seed, const int64_t *q_row_ptr, const int32_t *q_col, int64_t nq, int32_t k,
+                 uint64_t seed, uint32_t densify, const int64_t *q_row_ptr, const int32_t *q_col, int64_t nq, int32_t k,
                  const int32_t *exclude, int32_t *out_ids, int32_t *out_counts) {
   uint32_t B = K * L, t;
   uint64_t T = 1ULL << rb;
@@ -371,7 +397,7 @@ int oracle_query(const int32_t *tables, const uint32_t *counts, uint32_t K, uint
       for (e = 0; e < k; ++e) { out_ids[q * k + e] = -1; out_counts[q * k + e] = 0; }
       continue;
     }
-    doph_row(q_col + q_row_ptr[q], nnz, B, &s, all_hashes, v, filled, nx);
+    doph_row(q_col + q_row_ptr[q], nnz, B, &s, densify, all_hashes, v, filled, nx);
     for (t = 0; t < L; ++t) {                                  /* Append A with Table_t[Key_t] */
       uint32_t key = map_k_hashes_to_address(all_hashes, t, K, L, rb, &s);
       uint64_t bucket = (uint64_t)t * T + key;
@@ -424,7 +450,7 @@ int oracle_query_one_streamed(const uint32_t *keys_all, int64_t ld, const int64_
  * Every data point is a query against the index of all points, excluding
  * itself (Section 1; Section 4.3: Initialization + Addition + Querying).  */
 int oracle_knn_graph(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t K, uint32_t L, uint32_t R,
-                     uint32_t rb, uint64_t seed, int32_t k, int32_t *out_ids, int32_t *out_counts) {
+                     uint32_t rb, uint64_t seed, uint32_t densify, int32_t k, int32_t *out_ids, int32_t *out_counts) {
   uint64_t T = 1ULL << rb;
   int32_t *tables = (int32_t *)malloc(sizeof(int32_t) * (size_t)((uint64_t)L * T * R));
   uint32_t *counts = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)((uint64_t)L * T));
@@ -433,8 +459,9 @@ int oracle_knn_graph(const int64_t *row_ptr, const int32_t *col, int64_t n, uint
   int rc;
   if (!tables || !counts || !self) { free(tables); free(counts); free(self); return -1; }
   for (p = 0; p < n; ++p) self[p] = (int32_t)p;
-  rc = oracle_build(row_ptr, col, n, K, L, R, rb, seed, tables, counts);
-  if (rc == 0) rc = oracle_query(tables, counts, K, L, R, rb, seed, row_ptr, col, n, k, self, out_ids, out_counts);
+  rc = oracle_build(row_ptr, col, n, K, L, R, rb, seed, densify, tables, counts);
+  if (rc == 0)
+    rc = oracle_query(tables, counts, K, L, R, rb, seed, densify, row_ptr, col, n, k, self, out_ids, out_counts);
   free(tables);
   free(counts);
   free(self);

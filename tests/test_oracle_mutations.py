@@ -59,6 +59,13 @@ MUTATIONS = {
                               "test_candidate_count_total_is_the_gathered_reservoir_size"),
     "seed_not_forced_odd": ("s.a1 = splitmix64_next(&st) | 1ULL;", "s.a1 = splitmix64_next(&st) & ~1ULL;",
                             "test_seed_words_are_published_splitmix64_outputs"),
+    "optimal_copy_with_offset": ("      h[j] = v[src];\n", "      h[j] = v[src] + 0x9E3779B9u;\n",
+                                 "test_optimal_densification_copies_non_empty_bins"),
+    "optimal_probe_ignores_bin": ("splitmix64_mix(s->d ^ (((uint64_t)j << 32) | i))", "splitmix64_mix(s->d ^ i)",
+                                  "test_optimal_densification_picks_sources_independently_per_bin"),
+    "optimal_probe_ignores_attempt": ("splitmix64_mix(s->d ^ (((uint64_t)j << 32) | i))",
+                                      "splitmix64_mix(s->d ^ (((uint64_t)j << 32) | 1))",
+                                      "test_optimal_densification_picks_sources_independently_per_bin"),
 }
 
 

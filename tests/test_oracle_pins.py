@@ -119,6 +119,78 @@ def test_densification_closed_form_from_singletons():
         assert np.array_equal(oracle.doph(rp, col, K, L, seed)[0], exp)
 
 
+def _bins_and_values(elems, K, L, seed):
+    """Non-empty bin -> its OPH value (min in-bin value), from singletons and the rotation closed form."""
+    bins = {}
+    for e in elems:
+        h1 = _singleton(e, K, L, seed)
+        s = _source_bin_of_singleton(h1)
+        assert len(s) == 1
+        bins.setdefault(s[0], []).append(int(h1[s[0]]))
+    return {s: min(vals) for s, vals in bins.items()}
+
+
+def test_optimal_densification_copies_non_empty_bins():
+    """Optimal densification ([36], the variant Section 2.3 cites): a non-empty bin keeps its OPH
+    value and an empty bin takes the value of some non-empty bin, unchanged (no offset)."""
+    K, L = 4, 16
+    B = K * L
+    rng = np.random.default_rng(14)
+    for trial in range(40):
+        seed = 7100 + trial
+        elems = rand_set(rng, int(rng.integers(1, 6)))
+        v = _bins_and_values(elems, K, L, seed)
+        rp, col = csr_of([elems])
+        h = oracle.doph(rp, col, K, L, seed, densify=1)[0]
+        values = set(v.values())
+        for j in range(B):
+            if j in v:
+                assert h[j] == v[j]
+            else:
+                assert int(h[j]) in values
+
+
+def test_optimal_densification_picks_sources_independently_per_bin():
+    """Each empty bin draws its source by a hash of (bin, attempt), uniform over the bins: it
+    copies each of the f non-empty bins with probability 1/f, independently of its neighbours.
+    So the shares p_s of the empty bins copying s have E[sum_s p_s^2] = 1/f + (1 - 1/f)/n_empty,
+    and two adjacent empty bins copy the same source with probability sum_s p_s^2 (rotation's
+    copies run in long blocks instead: probability near 1)."""
+    K, L = 4, 64
+    B = K * L
+    rng = np.random.default_rng(15)
+    same, expect, uniform = [], [], []
+    for trial in range(60):
+        seed = 7300 + trial
+        elems = rand_set(rng, int(rng.integers(2, 6)))
+        v = _bins_and_values(elems, K, L, seed)
+        if len(set(v.values())) < 2:
+            continue
+        src_of_value = {val: s for s, val in v.items()}
+        rp, col = csr_of([elems])
+        h = oracle.doph(rp, col, K, L, seed, densify=1)[0]
+        src = [src_of_value[int(x)] for x in h]
+        empty = [j for j in range(B) if j not in v]
+        share = collections.Counter(src[j] for j in empty)
+        p = np.array(list(share.values()), dtype=float) / len(empty)
+        pairs = [(j, j + 1) for j in range(B - 1) if j not in v and j + 1 not in v]
+        same.append(np.mean([src[a] == src[b] for a, b in pairs]))
+        expect.append(float(np.sum(p ** 2)))
+        f = len(v)
+        uniform.append(1 / f + (1 - 1 / f) / len(empty))
+    assert len(same) >= 40
+    assert abs(np.mean(expect) - np.mean(uniform)) < 0.05, (np.mean(expect), np.mean(uniform))
+    assert abs(np.mean(same) - np.mean(expect)) < 0.08, (np.mean(same), np.mean(expect))
+
+
+def test_optimal_and_rotation_agree_when_every_bin_is_filled():
+    """With no empty bin there is nothing to densify: both variants are the OPH bins."""
+    rng = np.random.default_rng(16)
+    rows = [rand_set(rng, 4000) for _ in range(6)]
+    rp, col = csr_of(rows)
+    assert np.array_equal(oracle.doph(rp, col, 4, 8, seed=5, densify=0), oracle.doph(rp, col, 4, 8, seed=5, densify=1))
+
+
 def test_empty_row_hashes_all_ones():
     rp, col = csr_of([[], [5]])
     h = oracle.doph(rp, col, 2, 3, seed=9)
@@ -134,13 +206,13 @@ def _planted_pair(rng, a, e):
     return sorted(common + ex), sorted(common + ey), a / (a + 2 * e)
 
 
-@pytest.mark.parametrize("dense", [True, False])
+@pytest.mark.parametrize("dense,densify", [(True, 0), (False, 0), (False, 1)])
 @pytest.mark.parametrize("a_e", [(20, 90), (60, 70), (100, 50), (160, 20)])
-def test_bin_collision_rate_is_jaccard(dense, a_e):
+def test_bin_collision_rate_is_jaccard(dense, densify, a_e):
     """Eq. 2: Pr[h_j(x) = h_j(y)] = J(x, y) for every bin j.  Dense rows (all bins filled)
-    check OPH; rows much sparser than B check the densified bins (rotation keeps Eq. 2 exact for
-    a random permutation).  Tolerance: 4 standard errors of the per-pair mean + 0.01 for the
-    universal hash family standing in for a true permutation."""
+    check OPH; rows much sparser than B check the densified bins (rotation and optimal
+    densification both keep Eq. 2 exact for a random permutation).  Tolerance: 4 standard errors
+    of the per-pair mean + 0.01 for the universal hash family standing in for a true permutation."""
     a, e = a_e
     scale = 4 if dense else 0.1
     a, e = max(1, int(a * scale)), max(1, int(e * scale))
@@ -150,7 +222,7 @@ def test_bin_collision_rate_is_jaccard(dense, a_e):
     for trial in range(300):
         x, y, J = _planted_pair(rng, a, e)
         rp, col = csr_of([x, y])
-        h = oracle.doph(rp, col, K, L, seed=50_000 + trial)
+        h = oracle.doph(rp, col, K, L, seed=50_000 + trial, densify=densify)
         rates.append(np.mean(h[0] == h[1]))
         Js.append(J)
     J = Js[0]
