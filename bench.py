@@ -475,6 +475,25 @@ def main():
             "frac_of_hbm_peak": hash_bytes / (hash_ms / 1000.0) / 1e9 / peak,
             "bytes_formula": "8(N+1) + 4 nnz + 4 K L N", "keys_epilogue_GB/s": keys_bytes / (keys_ms / 1e3) / 1e9}
 
+    # the two densifications (rotation; optimal, [36]) on sparse kdd12-like rows, where most bins are empty
+    densify = None
+    if not args.rows and args.workload == "webspam_like":
+        from paper_1709_01190_gb300 import synth as _s
+        wk = _s.WORKLOADS["kdd12_like"].scaled(1_000_000)
+        ck = _s.generate(wk.data)
+        dk = fl.DeviceCSR.from_host(ck)
+        pk = wk.params
+        kout = torch.empty((pk.L, ck.n_rows), dtype=torch.int32, device="cuda")
+        dms = {}
+        for mode in (0, 1):
+            pm = fl.FlashParams(pk.K, pk.L, pk.R, pk.range_bits, pk.seed, densify=mode)
+            dms[mode] = timed(lambda: fl.flash_keys(pm, dk, kout, stream), 3)
+        densify = {"workload": f"kdd12-like rows: {ck.n_rows:,} rows, {ck.nnz:,} non-zeros, K={pk.K} L={pk.L} "
+                               f"(B={pk.K * pk.L}), flash_keys",
+                   "rotation_ms": dms[0], "optimal_ms": dms[1],
+                   "rotation_rows_per_s": ck.n_rows / (dms[0] / 1e3), "optimal_rows_per_s": ck.n_rows / (dms[1] / 1e3)}
+        del dk, kout
+
     e2e = None
     if not args.no_e2e:
         out_i = torch.empty((n, k), dtype=torch.int32, pin_memory=True).numpy()
@@ -509,7 +528,8 @@ def main():
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded, webspam-shaped; see config)",
                 "config": config_of(w, csr), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "phases_ms": acc, "doph": doph, "graph_replay_ms_per_step": graph_ms, "tuning": tuned,
+                "phases_ms": acc, "doph": doph, "densify": densify, "graph_replay_ms_per_step": graph_ms,
+                "tuning": tuned,
                 "served": served, "reduced": bool(args.rows)}
         print(json.dumps(line), flush=True)
     if world > 1:

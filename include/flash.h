@@ -66,6 +66,15 @@ typedef struct flash_params {
   uint32_t R;
   uint32_t range_bits;
   uint64_t seed;
+  /* Densification of the empty bins of a row (Section 2.3): 0 = rotation
+   * (Shrivastava & Li 2014: copy the next non-empty bin to the right plus
+   * distance * 0x9E3779B9), 1 = optimal densification (the paper's [36]:
+   * probe bins by a SplitMix64 mix of (bin, attempt) seeded from `seed`,
+   * copy the first non-empty one; after 8*K*L misses copy the next non-empty
+   * bin to the right).  Other values are FLASH_EINVAL.  Zero-initialised
+   * callers get rotation. */
+  uint32_t densify;
+  uint32_t reserved; /* must be 0 */
 } flash_params;
 
 /* A sparse matrix in CSR form; all pointers are DEVICE pointers.

@@ -36,15 +36,17 @@ def build(force: bool = False) -> str:
 @dataclasses.dataclass(frozen=True)
 class FlashParams:
     """K hashes per table, L tables (Section 2.2), reservoirs of R ids (Section 3.2),
-    2^range_bits buckets per table (Section 4.4.1), and the seed of every random choice."""
+    2^range_bits buckets per table (Section 4.4.1), the seed of every random choice, and the
+    densification of empty bins (Section 2.3): 0 rotation, 1 optimal densification ([36])."""
     K: int
     L: int
     R: int
     range_bits: int
     seed: int
+    densify: int = 0
 
     def c(self) -> Params:
-        return Params(self.K, self.L, self.R, self.range_bits, self.seed & ((1 << 64) - 1))
+        return Params(self.K, self.L, self.R, self.range_bits, self.seed & ((1 << 64) - 1), self.densify, 0)
 
     @property
     def B(self) -> int:

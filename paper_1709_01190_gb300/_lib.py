@@ -24,7 +24,8 @@ class FlashError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_uint32), ("L", ctypes.c_uint32), ("R", ctypes.c_uint32),
-                ("range_bits", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("range_bits", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("densify", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class Csr(ctypes.Structure):

@@ -16,7 +16,7 @@ namespace flash {
 //   a2, b2: universal map of a K-tuple to a bucket address    (Section 2.2)
 //   r     : key of the reservoir decisions                     (Algorithm 1)
 struct Seeds {
-  uint64_t a1, b1, a2, b2, r;
+  uint64_t a1, b1, a2, b2, r, d;  // d: key of the optimal-densification probes
 };
 
 __host__ __device__ inline uint64_t sm64_finalize(uint64_t z) {
@@ -27,8 +27,8 @@ __host__ __device__ inline uint64_t sm64_finalize(uint64_t z) {
 
 inline Seeds derive_seeds(uint64_t seed) {
   Seeds s;
-  uint64_t w[5];
-  for (int i = 0; i < 5; ++i) {
+  uint64_t w[6];
+  for (int i = 0; i < 6; ++i) {
     seed += 0x9E3779B97F4A7C15ULL;
     w[i] = sm64_finalize(seed);
   }
@@ -37,6 +37,7 @@ inline Seeds derive_seeds(uint64_t seed) {
   s.a2 = w[2] | 1ULL;
   s.b2 = w[3];
   s.r = w[4];
+  s.d = w[5];
   return s;
 }
 

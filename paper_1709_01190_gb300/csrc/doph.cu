@@ -23,7 +23,9 @@
 // Densification (rotation): word by word, lane l takes bin 32w + l; an empty
 // bin j becomes v[src] + (src - j) * 0x9E3779B9, src the first non-empty bin
 // after j, circularly (found from the word bitmap and a ballot summary of the
-// non-empty words).
+// non-empty words).  Optimal densification ([36]): an empty bin copies the
+// first non-empty bin of its own probe sequence (a SplitMix64 mix of (bin,
+// attempt)).
 // Emit: the B hashes (coalesced, 16-byte stores when aligned) or the L keys.
 #include <cuda_runtime.h>
 
@@ -43,6 +45,7 @@ struct DophParams {
   int64_t n_rows, nnz;
   uint32_t dim_u32;  // dim clipped to 2^32-1 (columns are int32)
   uint32_t B, K, L, rb, W, G;  // W = bitmap words, G = summary words
+  uint32_t densify;            // 0 rotation, 1 optimal densification
   uint32_t rows_per_grab;
   uint32_t smem_words_per_warp;
   Seeds s;
@@ -223,6 +226,44 @@ __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const u
   __syncwarp();
 }
 
+// Optimal densification ([36], cited in Section 2.3): an empty bin j probes
+// bins src_i = ((mix(d ^ (j * 2^32 + i)) >> 32) * B) >> 32, i = 1 .. 8B (mix =
+// SplitMix64's output function), and copies the first non-empty one; after 8B
+// misses it copies the first non-empty bin to its right, circularly.  Each
+// lane walks its own bins (lane, lane + 32, ...) so that the lanes' probe
+// counts even out over the row; only empty bins are written and only
+// non-empty ones read.
+__device__ __forceinline__ bool bin_filled(const uint32_t *mask, uint32_t b) { return (mask[b >> 5] >> (b & 31)) & 1u; }
+
+__device__ __noinline__ void optimal_densify(const DophParams &a, uint32_t *bins, const uint32_t *mask,
+                                             uint32_t lane) {
+  const uint32_t B = a.B;
+  for (uint32_t j = lane; j < B; j += 32) {
+    if (bin_filled(mask, j)) continue;
+    uint32_t src = 0xFFFFFFFFu;
+    for (uint32_t i = 1; i <= 8u * B; ++i) {
+      const uint64_t u = sm64_finalize(a.s.d ^ ((static_cast<uint64_t>(j) << 32) | i));
+      const uint32_t probe = static_cast<uint32_t>(((u >> 32) * B) >> 32);
+      if (bin_filled(mask, probe)) {
+        src = probe;
+        break;
+      }
+    }
+    if (src == 0xFFFFFFFFu) {  // the next non-empty bin to the right, circularly (one exists)
+      src = j;
+      for (uint32_t t = 1; t <= B; ++t) {
+        const uint32_t b = j + t < B ? j + t : j + t - B;
+        if (bin_filled(mask, b)) {
+          src = b;
+          break;
+        }
+      }
+    }
+    bins[j] = bins[src];
+  }
+  __syncwarp();
+}
+
 // Densification by rotation and the emit of row r (keys or hashes).
 template <bool KEYS>
 __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint32_t *bins, const uint32_t *mask,
@@ -243,7 +284,9 @@ __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint3
     __syncwarp();
     return;
   }
-  if (filled < B) {
+  if (filled < B && a.densify) {
+    optimal_densify(a, bins, mask, lane);
+  } else if (filled < B) {
     // word by word, lane l takes bin 32w + l: the words and the next non-empty
     // word are warp-uniform (broadcast reads), bins are consecutive per lane
     // (no bank conflicts).  An empty bin j copies the first non-empty bin
@@ -498,6 +541,7 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.G = (a.W + 31) / 32;
   a.smem_words_per_warp = a.W * 32 + ((a.W + 3) & ~3u);
   a.s = L.seeds;
+  a.densify = L.densify;
   a.out = L.out;
   a.out_rm = L.out_rowmajor;
   a.ld = L.ld;

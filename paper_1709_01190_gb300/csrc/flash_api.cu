@@ -147,6 +147,7 @@ class Arena {
 
 int check_hash_params(const flash_params *p) {
   if (!p || p->K < 1 || p->L < 1) return FLASH_EINVAL;
+  if (p->densify > 1 || p->reserved != 0) return FLASH_EINVAL;
   if (static_cast<uint64_t>(p->K) * p->L > kMaxBins) return FLASH_EINVAL;
   return 0;
 }
@@ -180,6 +181,7 @@ DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, 
   d.K = p->K;
   d.L = p->L;
   d.range_bits = p->range_bits;
+  d.densify = p->densify;
   d.seeds = s;
   d.keys = keys;
   d.out = out;

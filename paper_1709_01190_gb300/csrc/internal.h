@@ -30,6 +30,7 @@ struct DophLaunch {
   const int32_t *col;
   int64_t n_rows, nnz, dim;
   uint32_t K, L, range_bits;
+  uint32_t densify;  // 0 rotation, 1 optimal densification
   Seeds seeds;
   bool keys;         // false: out = hashes [n_rows][K*L]; true: out = keys [L][ld] (or null)
   uint32_t *out;

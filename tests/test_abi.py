@@ -47,6 +47,8 @@ def test_host_only_helpers(libflash):
     need = fl.flash_knn_graph_scratch_bytes(p, 350_000)
     assert need >= 5 * 4 * 64 * 350_000  # keys, sorted keys, sort ping-pong, ids
     assert fl.flash_knn_graph_scratch_bytes(fl.FlashParams(0, 1, 1, 1, 1), 10) == 0
+    assert fl.flash_knn_graph_scratch_bytes(fl.FlashParams(4, 64, 64, 18, 1, densify=1), 10) > 0
+    assert fl.flash_knn_graph_scratch_bytes(fl.FlashParams(4, 64, 64, 18, 1, densify=2), 10) == 0
     old = fl.flash_set_scratch_budget(123)
     assert fl.flash_set_scratch_budget(old) == 123
 

@@ -100,6 +100,49 @@ def test_doph_long_rows_every_length_class(order):
     assert fl.flash_device_error() == 0
 
 
+# ---------------------------------------------- optimal densification ([36])
+
+@pytest.mark.parametrize("K,L", [(1, 1), (3, 5), (4, 16), (2, 33), (4, 256), (8, 512)])
+def test_doph_optimal_densification_adversarial(K, L):
+    B = K * L
+    rng = np.random.default_rng(B + 5)
+    dim = 1 << 24
+    c = csr_of(adversarial_rows(rng, B, dim), dim)
+    p = fl.FlashParams(K, L, 4, 10, 0xABCDEF + B, densify=1)
+    got = u32(fl.hash_rows(p, fl.DeviceCSR.from_host(c)))
+    assert np.array_equal(got, oracle.doph(c.row_ptr, c.col, K, L, p.seed, densify=1))
+    assert fl.flash_device_error() == 0
+
+
+@pytest.mark.parametrize("name,n", [("kdd12_like", 20_000), ("url_like_batched", 4_000), ("tiny_plain", 3_000)])
+def test_doph_optimal_densification_workloads(name, n):
+    """Sparse rows (kdd12-like: about 12 non-zeros in 1,024 bins) densify most bins."""
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p0 = params_of(w)
+    p = fl.FlashParams(p0.K, p0.L, p0.R, p0.range_bits, p0.seed, densify=1)
+    dev = fl.DeviceCSR.from_host(c)
+    got = u32(fl.hash_rows(p, dev))
+    assert np.array_equal(got, oracle.doph(c.row_ptr, c.col, p.K, p.L, p.seed, densify=1))
+    keys = fl.row_keys(p, dev).cpu().numpy().view(np.uint32)
+    ek = oracle.keys(c.row_ptr, c.col, p.K, p.L, p.range_bits, p.seed, densify=1)
+    ek[:, np.diff(c.row_ptr) == 0] = 1 << p.range_bits
+    assert np.array_equal(keys, ek)
+
+
+@pytest.mark.parametrize("name,n,over", [("kdd12_like", 15_000, dict(range_bits=13, L=64)),
+                                         ("tiny_plain", 6_000, None)])
+def test_knn_graph_optimal_densification(name, n, over):
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p0 = _params_override(w, over)
+    p = fl.FlashParams(p0.K, p0.L, p0.R, p0.range_bits, p0.seed, densify=1)
+    ids, cnt = fl.knn_graph(p, fl.DeviceCSR.from_host(c), w.k)
+    ei, en = oracle.knn_graph(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, w.k, densify=1)
+    assert np.array_equal(ids.cpu().numpy(), ei)
+    assert np.array_equal(cnt.cpu().numpy(), en)
+
+
 def test_doph_column_array_not_16_byte_aligned():
     """A column array starting 4, 8 or 12 bytes past a 16-byte boundary (a slice): the
     kernels find each row's 16-byte body from the actual address; a pointer that is not
@@ -325,7 +368,7 @@ def test_invalid_parameters_are_rejected_on_the_host():
     out = torch.empty((2, 4), dtype=torch.int32, device="cuda")
     for bad in (fl.FlashParams(0, 4, 4, 8, 1), fl.FlashParams(4, 0, 4, 8, 1), fl.FlashParams(4, 4, 0, 8, 1),
                 fl.FlashParams(4, 4, 4, 0, 1), fl.FlashParams(4, 4, 4, 31, 1), fl.FlashParams(64, 128, 1, 8, 1),
-                fl.FlashParams(1, 300, 2, 8, 1)):
+                fl.FlashParams(1, 300, 2, 8, 1), fl.FlashParams(4, 4, 4, 8, 1, densify=2)):
         with pytest.raises(fl.FlashError) as e:
             fl.flash_knn_graph(bad, c, 4, out, out.clone())
         assert e.value.code == 1
