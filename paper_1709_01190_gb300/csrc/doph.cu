@@ -235,19 +235,26 @@ __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const u
 // non-empty ones read.
 __device__ __forceinline__ bool bin_filled(const uint32_t *mask, uint32_t b) { return (mask[b >> 5] >> (b & 31)) & 1u; }
 
-__device__ __noinline__ void optimal_densify(const DophParams &a, uint32_t *bins, const uint32_t *mask,
+__device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mask, uint32_t B, uint64_t d,
                                              uint32_t lane) {
-  const uint32_t B = a.B;
+  const uint32_t imax = 8u * B;  // a multiple of 4
   for (uint32_t j = lane; j < B; j += 32) {
     if (bin_filled(mask, j)) continue;
     uint32_t src = 0xFFFFFFFFu;
-    for (uint32_t i = 1; i <= 8u * B; ++i) {
-      const uint64_t u = sm64_finalize(a.s.d ^ ((static_cast<uint64_t>(j) << 32) | i));
-      const uint32_t probe = static_cast<uint32_t>(((u >> 32) * B) >> 32);
-      if (bin_filled(mask, probe)) {
-        src = probe;
-        break;
+    const uint64_t key = d ^ (static_cast<uint64_t>(j) << 32);  // d ^ (j * 2^32 + i) = key ^ i for i < 2^32
+    // four probes at a time (independent mixes), the earliest hit wins
+    for (uint32_t i = 1; i <= imax && src == 0xFFFFFFFFu; i += 4) {
+      uint32_t pr[4];
+      bool hit[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t u = sm64_finalize(key ^ static_cast<uint64_t>(i + q));
+        pr[q] = static_cast<uint32_t>(((u >> 32) * B) >> 32);
+        hit[q] = bin_filled(mask, pr[q]);
       }
+#pragma unroll
+      for (int q = 3; q >= 0; --q)
+        if (hit[q]) src = pr[q];
     }
     if (src == 0xFFFFFFFFu) {  // the next non-empty bin to the right, circularly (one exists)
       src = j;
@@ -285,7 +292,7 @@ __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint3
     return;
   }
   if (filled < B && a.densify) {
-    optimal_densify(a, bins, mask, lane);
+    optimal_densify(bins, mask, a.B, a.s.d, lane);
   } else if (filled < B) {
     // word by word, lane l takes bin 32w + l: the words and the next non-empty
     // word are warp-uniform (broadcast reads), bins are consecutive per lane
