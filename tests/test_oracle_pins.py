@@ -183,6 +183,23 @@ def test_optimal_densification_picks_sources_independently_per_bin():
     assert abs(np.mean(same) - np.mean(expect)) < 0.08, (np.mean(same), np.mean(expect))
 
 
+@pytest.mark.parametrize("a_e", [(6, 6), (3, 10)])
+def test_optimal_densification_lowers_the_variance_of_the_jaccard_estimate(a_e):
+    """[36]'s point: with very sparse rows, rotation copies one non-empty bin into long runs of
+    empty ones, so the fraction of matching bins (the estimate of J) varies much more than
+    when every empty bin draws its own source.  Both stay unbiased (Eq. 2, pinned above)."""
+    a, e = a_e
+    rng = np.random.default_rng(20 + a)
+    est = {0: [], 1: []}
+    for trial in range(300):
+        x, y, J = _planted_pair(rng, a, e)
+        rp, col = csr_of([x, y])
+        for d in (0, 1):
+            h = oracle.doph(rp, col, 4, 64, seed=60_000 + trial, densify=d)
+            est[d].append(np.mean(h[0] == h[1]))
+    assert np.var(est[1]) < np.var(est[0]) / 3, (np.var(est[1]), np.var(est[0]))
+
+
 def test_optimal_and_rotation_agree_when_every_bin_is_filled():
     """With no empty bin there is nothing to densify: both variants are the OPH bins."""
     rng = np.random.default_rng(16)
