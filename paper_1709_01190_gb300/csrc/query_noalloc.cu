@@ -96,6 +96,7 @@ extern "C" int flash_query_noalloc(const flash_index *ix, const flash_csr *q, in
   d.K = p->K;
   d.L = p->L;
   d.range_bits = p->range_bits;
+  d.densify = p->densify;
   d.seeds = ix->s;
   d.keys = true;
   d.out = qkeys;

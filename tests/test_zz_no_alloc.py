@@ -75,3 +75,28 @@ def test_noalloc_query_rejects_batches_beyond_its_scratch(index_and_queries):
                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 1  # FLASH_EINVAL, nothing launched
     assert fl.flash_device_error() == 0
+
+
+def test_noalloc_query_keeps_the_index_densification():
+    """An index built with optimal densification hashes its queries the same way."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    fl.build()
+    w = synth.WORKLOADS["kdd12_like"].scaled(8_000)
+    c = synth.generate(w.data)
+    p = w.params
+    params = fl.FlashParams(p.K, 32, p.R, 12, p.seed, densify=1)
+    ix = fl.flash_build(params, fl.DeviceCSR.from_host(c))
+    q = c.rows(synth.sample_rows(c.n_rows, 500, seed=4))
+    dq = fl.DeviceCSR.from_host(q)
+    got = _noalloc(ix, dq, w.k)
+    exp = fl.query(ix, dq, w.k)
+    torch.cuda.synchronize()
+    assert torch.equal(got[0], exp[0]) and torch.equal(got[1], exp[1])
+    et, ec = oracle.build_tables(c.row_ptr, c.col, params.K, params.L, params.R, params.range_bits, params.seed,
+                                 densify=1)
+    ei, en = oracle.query(et, ec, params.K, params.L, params.R, params.range_bits, params.seed, q.row_ptr, q.col,
+                          w.k, densify=1)
+    assert np.array_equal(got[0].cpu().numpy(), ei) and np.array_equal(got[1].cpu().numpy(), en)
+    ix.free()
