@@ -106,9 +106,11 @@ typedef struct flash_index_info {
 /* DOPH (Section 2.3 on the minwise hash of Eq. 1): K*L hashes per row.
  *   hashes : DEVICE uint32 [n_rows][K*L], row-major.
  * Bin j of row r is the smallest in-bin offset of the row's columns under one
- * permutation split into K*L equal ranges; empty bins are densified by
- * rotation (first non-empty bin to the right at distance t, plus
- * t*0x9E3779B9).  A row with no entries hashes to 0xFFFFFFFF everywhere. */
+ * permutation split into K*L equal ranges; empty bins are densified as
+ * p->densify selects: rotation (first non-empty bin to the right at distance
+ * t, plus t*0x9E3779B9) or optimal densification (the first non-empty bin of
+ * the bin's own probe sequence, copied).  A row with no entries hashes to
+ * 0xFFFFFFFF everywhere. */
 int flash_hash(const flash_params *p, const flash_csr *x, uint32_t *hashes, void *stream);
 
 /* MapKHashesToAddress (Section 2.2, Algorithm 2) fused after DOPH: the L
