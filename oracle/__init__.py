@@ -51,6 +51,7 @@ def _lib():
         lib.oracle_hash.argtypes = [_P, _P, _I64, _I64, _U32, _U32, _U64, _U32, _P]
         lib.oracle_keys.argtypes = [_P, _P, _I64, _I64, _U32, _U32, _U32, _U64, _U32, _P, _I64]
         lib.oracle_build.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _U32, _P, _P]
+        lib.oracle_add.argtypes = [_P, _P, _I64, _I32, _U32, _U32, _U32, _U32, _U64, _U32, _P, _P]
         lib.oracle_bucket.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U64, _P, _P]
         lib.oracle_kselect.argtypes = [_P, _I64, _I32, _I32, _P, _P]
         lib.oracle_query.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _U64, _U32, _P, _P, _I64, _I32, _P, _P, _P]
@@ -151,6 +152,17 @@ def build_tables(row_ptr, col, K, L, R, range_bits, seed, densify=0):
     _check(_lib().oracle_build(prp, pcl, n, K, L, R, range_bits, seed, densify, tables.ctypes.data,
                                counts.ctypes.data))
     return tables, counts
+
+
+def add_rows(tables, counts, row_ptr, col, id0, K, L, R, range_bits, seed, densify=0):
+    """Algorithm 2 continued: ADD rows [0, n) of (row_ptr, col) as points id0 + row into the
+    given tables / counts (int32 [L][2^rb][R], uint32 [L][2^rb]), in place."""
+    rp, prp = _c(row_ptr, np.int64)
+    cl, pcl = _c(col, np.int32)
+    assert tables.dtype == np.int32 and counts.dtype == np.uint32
+    assert tables.flags.c_contiguous and counts.flags.c_contiguous
+    _check(_lib().oracle_add(prp, pcl if cl.size else None, rp.shape[0] - 1, id0, K, L, R, range_bits, seed, densify,
+                             tables.ctypes.data, counts.ctypes.data))
 
 
 def bucket(keys_t, row_ptr, t, key, R, seed):

@@ -241,8 +241,23 @@ int oracle_keys(const int64_t *row_ptr, const int32_t *col, int64_t r0, int64_t 
  * tables[(t * 2^rb + key) * R + slot] (empty slot = -1),
  * counts[t * 2^rb + key] = number of arrivals (not capped at R).
  * Reading: a row with no non-zeros is not inserted anywhere.              */
+int oracle_add(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t id0, uint32_t K, uint32_t L,
+               uint32_t R, uint32_t rb, uint64_t seed, uint32_t densify, int32_t *tables, uint32_t *counts);
+
 int oracle_build(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t K, uint32_t L, uint32_t R,
                  uint32_t rb, uint64_t seed, uint32_t densify, int32_t *tables, uint32_t *counts) {
+  uint64_t T = 1ULL << rb, z;
+  for (z = 0; z < (uint64_t)L * T * R; ++z) tables[z] = -1;
+  memset(counts, 0, sizeof(uint32_t) * (size_t)((uint64_t)L * T));
+  return oracle_add(row_ptr, col, n, 0, K, L, R, rb, seed, densify, tables, counts);
+}
+
+/* Algorithm 2 is a stream: ADD continues every bucket's arrival count, so
+ * points added later (rows [0, n) of another matrix, point ids id0 + row)
+ * extend tables and counts exactly as if they had come after the earlier
+ * points in one build.                                                     */
+int oracle_add(const int64_t *row_ptr, const int32_t *col, int64_t n, int32_t id0, uint32_t K, uint32_t L,
+               uint32_t R, uint32_t rb, uint64_t seed, uint32_t densify, int32_t *tables, uint32_t *counts) {
   uint32_t B = K * L, t;
   uint64_t T = 1ULL << rb;
   oracle_seeds_t s = make_seeds(seed);
@@ -251,10 +266,7 @@ int oracle_build(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t
   uint8_t *filled = (uint8_t *)malloc(B);
   uint32_t *nx = (uint32_t *)malloc(sizeof(uint32_t) * B);
   int64_t p;
-  uint64_t z;
   if (!all_hashes || !v || !filled || !nx) { free(all_hashes); free(v); free(filled); free(nx); return -1; }
-  for (z = 0; z < (uint64_t)L * T * R; ++z) tables[z] = -1;
-  memset(counts, 0, sizeof(uint32_t) * (size_t)((uint64_t)L * T));
   for (p = 0; p < n; ++p) {                                   /* for each DataPoint */
     int64_t nnz = row_ptr[p + 1] - row_ptr[p];
     if (nnz == 0) continue;
@@ -262,7 +274,7 @@ int oracle_build(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t
     for (t = 0; t < L; ++t) {                                 /* for each Table_t */
       uint32_t key = map_k_hashes_to_address(all_hashes, t, K, L, rb, &s);
       uint64_t bucket = (uint64_t)t * T + key;
-      add(tables + bucket * R, counts + bucket, R, s.r, t, key, (int32_t)p);   /* ADD */
+      add(tables + bucket * R, counts + bucket, R, s.r, t, key, (int32_t)(id0 + p));   /* ADD */
     }
   }
   free(all_hashes);

@@ -526,3 +526,20 @@ def test_address_map_is_universal_on_k_tuples():
         same = sum(oracle.address(h, 1, K, L, rb, s) == oracle.address(g, 1, K, L, rb, s) for s in range(n_seeds))
         p = 2.0 ** -rb
         assert same <= n_seeds * 2 * p + 4 * math.sqrt(n_seeds * 2 * p), same
+
+
+def test_adding_in_batches_continues_every_bucket_stream():
+    """Algorithm 2 is a stream: tables built from the first rows, then extended by ADD with the
+    rest (point ids continuing), equal the tables of one build over all rows -- the arrival
+    counts continue, so every later reservoir draw uses the same rank as in one pass."""
+    from paper_1709_01190_gb300 import synth
+    w = synth.WORKLOADS["tiny_plain"].scaled(2_000)
+    c = synth.generate(w.data)
+    K, L, R, rb, seed = 3, 8, 4, 6, 11  # few buckets: every reservoir overflows
+    et, ec = oracle.build_tables(c.row_ptr, c.col, K, L, R, rb, seed)
+    for cut in (1, 700, 1999):
+        t, n = oracle.build_tables(c.row_ptr[:cut + 1], c.col[:c.row_ptr[cut]], K, L, R, rb, seed)
+        rp2 = c.row_ptr[cut:] - c.row_ptr[cut]
+        oracle.add_rows(t, n, rp2, c.col[c.row_ptr[cut]:], cut, K, L, R, rb, seed)
+        assert np.array_equal(t, et) and np.array_equal(n, ec), cut
+    assert ec.max() > 4 * R
