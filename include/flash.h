@@ -57,7 +57,7 @@ enum {
 
 /* Method parameters (Section 2.2: K hashes per meta-hash, L tables;
  * Section 3.2: reservoirs of size R; Section 4.4.1: 2^range_bits buckets
- * per table).  Limits of this build: K, L, R >= 1; K*L <= 4096;
+ * per table).  Limits of the library: K, L, R >= 1; K*L <= 4096;
  * 1 <= range_bits <= 30; L*R <= 16384 (count table of one query); L <= 256
  * and n_rows < 2^24 - 1 for the packed (id, count) query table. */
 typedef struct flash_params {

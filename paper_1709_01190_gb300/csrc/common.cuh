@@ -46,7 +46,7 @@ constexpr uint32_t kRotStep = 0x9E3779B9u;
 // Hash of every bin of a row without entries.
 constexpr uint32_t kEmptyHash = 0xFFFFFFFFu;
 
-// Limits of this build (checked on the host before any launch).
+// Implementation limits (checked on the host before any launch).
 constexpr uint32_t kMaxBins = 4096;        // K*L
 constexpr uint32_t kMaxRangeBits = 30;
 constexpr uint32_t kMaxCandidates = 16384; // L*R
