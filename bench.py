@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement (url-like index)")
     ap.add_argument("--no-tune", action="store_true", help="skip autotuning of the launch knobs")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="seconds per serving load point and repeat")
+    ap.add_argument("--no-url", action="store_true", help="skip the url-like batch and serving sections")
+    ap.add_argument("--no-kdd12", action="store_true", help="skip the kdd12-like graph section")
     return ap.parse_args()
 
 
@@ -182,27 +185,132 @@ def cpu_baseline(w, csr, target_s: float) -> dict:
                               "sample": f"first {n_st} rows, single-threaded C oracle, {t_st:.1f} s"}}
 
 
-def serving_measurement(fl, seconds_per_load: float = 1.5) -> dict:
-    """Served p50/p99 and queries/s on the url-like index (resident), requests of U[1, 4096] query rows."""
-    import threading
+def _timed(fn, reps, stream=None):
+    """Mean device milliseconds of fn() over reps calls (CUDA events on the launching stream)."""
     import torch
-    from paper_1709_01190_gb300 import serve, synth
-    w = synth.WORKLOADS["serving_url"]
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _phases(fl, fn, reps):
+    """Mean per-phase device milliseconds of fn() (events recorded between the library's phases)."""
+    fl.flash_enable_phase_timing(True)
+    acc = {}
+    try:
+        for _ in range(reps):
+            fn()
+            for name, v in fl.flash_phase_times().items():
+                acc[name] = acc.get(name, 0.0) + v / reps
+    finally:
+        fl.flash_enable_phase_timing(False)
+    return acc
+
+
+def _candidates(fl, ix, keys, R):
+    """Sum over queries and tables of min(m_t, R): the reservoir ids the queries gather (for the
+    query kernel's algorithmic bytes); keys int32 [L][nq] from flash_keys."""
+    import torch
+    p = ix.params
+    T = 1 << p.range_bits
+    tables = torch.empty((p.L, T, p.R), dtype=torch.int32, device="cuda")
+    counts = torch.empty((p.L, T), dtype=torch.int32, device="cuda")
+    fl.flash_index_export(ix, tables, counts)
+    del tables
+    total = 0
+    for t in range(p.L):
+        k = keys[t].long()
+        c = counts[t][k.clamp(max=T - 1)].clamp(max=R).long()
+        total += int(torch.where(k < T, c, torch.zeros_like(c)).sum())
+    del counts
+    torch.cuda.empty_cache()
+    return total
+
+
+def _peak(kind="hbm"):
+    peaks = measured_peaks()
+    v = peaks.get("hbm_gbs")
+    return (v, "measured (MEASURED_PEAKS.json hbm_gbs)") if v else (6800.0, "fallback")
+
+
+def url_section(fl, args, tune: bool) -> tuple[dict, dict]:
+    """The url-like index (2.4M rows, L=128, R=128, 2^15 buckets) resident on the device:
+    the 1,000,000-query batch (one call: untuned, autotuned, CUDA-graph captured) and the serving loop."""
+    import torch
+    from paper_1709_01190_gb300 import synth, tuning
+    w = synth.WORKLOADS["url_like_batched"]
     p = w.params
     params = fl.FlashParams(p.K, p.L, p.R, p.range_bits, p.seed)
     data = synth.generate(w.data)
     dev_data = fl.DeviceCSR.from_host(data)
-    fl.flash_build(params, dev_data).free()  # warm-up build
-    torch.cuda.synchronize()
-    a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record()
+    build_ms = _timed(lambda: fl.flash_build(params, dev_data).free(), 3)
     ix = fl.flash_build(params, dev_data)
-    b0.record()
     torch.cuda.synchronize()
-    build_ms = a0.elapsed_time(b0)
-    del dev_data
-    dim = data.dim
-    del data
+    n_rows, dim = data.n_rows, data.dim
+    del dev_data, data
+    qc = synth.generate(w.query_data)
+    dq = fl.DeviceCSR.from_host(qc)
+    k = w.k
+    ids = torch.empty((qc.n_rows, k), dtype=torch.int32, device="cuda")
+    cnt = torch.empty_like(ids)
+    stream = torch.cuda.current_stream()
+
+    def q_call():
+        fl.flash_query(ix, dq, k, None, ids, cnt, stream)
+
+    tuning.set_tuning(None)
+    plain_ms = _timed(q_call, 3)
+    ph = _phases(fl, q_call, 3)
+    tuned = None
+    tuned_ms = plain_ms
+    if tune:
+        key = tuning.shape_key("query", params, n_rows, 0, k, q_rows=qc.n_rows)
+        best, _ = tuning.autotune(q_call, key=key, reps=2)
+        tuned = dataclasses.asdict(best)
+        tuned_ms = _timed(q_call, 3)
+    g = tuning.GraphedQuery(ix, dq, k, None, ids, cnt)
+    graph_ms = _timed(g.replay, 5)
+    tuned_ph = _phases(fl, q_call, 3)
+    del g
+    tuning.set_tuning(None)
+    qkeys = fl.row_keys(params, dq)
+    m_total = _candidates(fl, ix, qkeys, p.R)
+    del qkeys
+    nq = qc.n_rows
+    qbytes = 4 * p.L * nq + 4 * m_total + 8 * k * nq
+    qms = tuned_ph.get("query", ph.get("query"))
+    peak, src = _peak()
+    c3 = {"workload": w.name, "index_rows": n_rows, "queries": nq, "k": k, "index_build_ms": build_ms,
+          "one_call_ms": plain_ms, "one_call_queries_per_s": nq / (plain_ms / 1e3),
+          "tuned": tuned, "tuned_ms": tuned_ms, "tuned_queries_per_s": nq / (tuned_ms / 1e3),
+          "graph_replay_ms": graph_ms, "graph_replay_queries_per_s": nq / (graph_ms / 1e3),
+          "phases_ms_untuned": ph, "phases_ms_tuned": tuned_ph,
+          "candidates_per_query": m_total / nq,
+          "query_roofline": {"kernel": "query kernels (gather, count, top-k) of the tuned call", "bound": "hbm",
+                             "algorithmic_bytes": qbytes,
+                             "bytes_formula": "sum over queries of sum_t (4 + 4 min(m_t, R)) + 8k",
+                             "duration_ms": qms, "achieved": qbytes / (qms / 1e3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": qbytes / (qms / 1e3) / 1e9 / peak, "peak_source": src}}
+    del dq, ids, cnt
+    torch.cuda.empty_cache()
+    served = None
+    if not args.no_serve:
+        served = serving_measurement(fl, ix, dim, args.serve_seconds)
+    ix.free()
+    return c3, served
+
+
+def serving_measurement(fl, ix, dim, seconds_per_load: float = 10.0, repeats: int = 3) -> dict:
+    """Served p50/p99 and queries/s on the resident url-like index, requests of U[1, 4096] query rows."""
+    import threading
+    from paper_1709_01190_gb300 import serve, synth
+    w = synth.WORKLOADS["serving_url"]
     qc = synth.generate(w.query_data)
     rng = np.random.default_rng(5)
     reqs, r0 = [], 0
@@ -215,22 +323,8 @@ def serving_measurement(fl, seconds_per_load: float = 1.5) -> dict:
         r0 += s
     mean_rows = float(np.mean([rp.shape[0] - 1 for rp, _ in reqs]))
     k = w.k
-    out = {"workload": w.name, "index_rows": int(ix.n_rows), "index_build_ms": build_ms, "k": k, "slots": 4,
-           "mem_budget_bytes": 8 << 30}
-
-    # one launch over all 1,000,000 query rows (the batched form), device-timed
-    d_q = fl.DeviceCSR.from_host(qc)
-    ids = torch.empty((qc.n_rows, k), dtype=torch.int32, device="cuda")
-    cnt = torch.empty_like(ids)
-    fl.flash_query(ix, d_q, k, None, ids, cnt)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    fl.flash_query(ix, d_q, k, None, ids, cnt)
-    b.record()
-    torch.cuda.synchronize()
-    out["one_launch_queries_per_s"] = qc.n_rows / (a.elapsed_time(b) / 1e3)
-    del d_q, ids, cnt
+    out = {"workload": w.name, "index_rows": int(ix.n_rows), "k": k, "slots": 4, "mem_budget_bytes": 8 << 30,
+           "seconds_per_load": seconds_per_load, "repeats": repeats}
 
     def server():
         return serve.Server(serve.CudaBackend(ix, k, dim, n_slots=4), mem_budget=8 << 30, max_batch_rows=16384)
@@ -241,7 +335,7 @@ def serving_measurement(fl, seconds_per_load: float = 1.5) -> dict:
         t.wait(120)
     srv.close()
     srv = server()
-    n_sat = min(len(reqs), 160)
+    n_sat = min(len(reqs), 240)
     t0 = time.perf_counter()
     ts = [srv.submit(*r) for r in reqs[:n_sat]]
     for t in ts:
@@ -253,52 +347,133 @@ def serving_measurement(fl, seconds_per_load: float = 1.5) -> dict:
     out["saturated_batches"] = srv.stats()["batches"]
 
     # plain path: one request at a time, one stream, copy in / query / copy out / wait
-    n_plain = min(len(reqs), 40)
+    n_plain = min(len(reqs), 200)
     serve.plain_serve(ix, k, reqs[:2], dim)
     t0 = time.perf_counter()
     serve.plain_serve(ix, k, reqs[:n_plain], dim)
     plain_s = time.perf_counter() - t0
     out["plain_queries_per_s"] = sum(r[0].shape[0] - 1 for r in reqs[:n_plain]) / plain_s
+    out["plain_requests"] = n_plain
 
-    # open loop: Poisson arrivals at fractions of the saturated rate
+    # open loop: Poisson arrivals at fractions of the saturated rate, several repeats per load
     loads = {}
     pos = n_sat
     for load in (0.25, 0.5, 0.8, 1.0):
         rate = load * out["saturated_queries_per_s"] / mean_rows  # requests per second
-        srv = server()
-        stop = time.perf_counter() + seconds_per_load
-        arng = np.random.default_rng(int(load * 100))
-        sent = []
+        reps = []
+        for rep in range(repeats):
+            srv = server()
+            stop = time.perf_counter() + seconds_per_load
+            arng = np.random.default_rng(int(load * 100) + 1000 * rep)
+            sent = []
 
-        def gen():
-            nonlocal pos
-            t_next = time.perf_counter()
-            while time.perf_counter() < stop and pos < len(reqs):
-                t_next += arng.exponential(1.0 / rate)
-                dt = t_next - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                sent.append(srv.submit(*reqs[pos]))
-                pos += 1
+            def gen():
+                nonlocal pos
+                t_next = time.perf_counter()
+                while time.perf_counter() < stop:
+                    t_next += arng.exponential(1.0 / rate)
+                    dt = t_next - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    if pos >= len(reqs):
+                        pos = n_sat
+                    sent.append(srv.submit(*reqs[pos]))
+                    pos += 1
 
-        th = threading.Thread(target=gen)
-        t0 = time.perf_counter()
-        th.start()
-        th.join()
-        for t in sent:
-            t.wait(300)
-        wall = time.perf_counter() - t0
-        srv.close()
-        st = srv.stats()
+            th = threading.Thread(target=gen)
+            t0 = time.perf_counter()
+            th.start()
+            th.join()
+            for t in sent:
+                t.wait(300)
+            wall = time.perf_counter() - t0
+            srv.close()
+            st = srv.stats()
+            reps.append({"served_queries_per_s": st["rows"] / wall, "p50_ms": st.get("p50_ms"),
+                         "p99_ms": st.get("p99_ms"), "requests": st["requests"], "batches": st["batches"]})
+        p99s = [r["p99_ms"] for r in reps if r["p99_ms"] is not None]
         loads[str(load)] = {"offered_queries_per_s": load * out["saturated_queries_per_s"],
-                            "served_queries_per_s": st["rows"] / wall, "p50_ms": st.get("p50_ms"),
-                            "p99_ms": st.get("p99_ms"), "requests": st["requests"], "batches": st["batches"]}
-        if pos >= len(reqs):
-            pos = n_sat
+                            "served_queries_per_s": float(np.median([r["served_queries_per_s"] for r in reps])),
+                            "p50_ms": float(np.median([r["p50_ms"] for r in reps if r["p50_ms"] is not None])),
+                            "p99_ms": float(np.median(p99s)) if p99s else None,
+                            "p99_ms_range": [min(p99s), max(p99s)] if p99s else None,
+                            "requests": sum(r["requests"] for r in reps), "repeats": reps}
     out["poisson"] = loads
     out["mean_request_rows"] = mean_rows
-    ix.free()
     return out
+
+
+def kdd12_section(fl, args) -> dict:
+    """The kdd12-like all-points k-NN graph (10M rows, L=256, R=32, 2^20 buckets, k=32): per-phase
+    times with their rooflines, and the plain unbatched path beside it."""
+    import torch
+    from paper_1709_01190_gb300 import synth
+    w = synth.WORKLOADS["kdd12_like"]
+    p = w.params
+    params = fl.FlashParams(p.K, p.L, p.R, p.range_bits, p.seed)
+    c = synth.generate(w.data)
+    dev = fl.DeviceCSR.from_host(c)
+    n, nnz, k = c.n_rows, c.nnz, w.k
+    del c
+    ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    cnt = torch.empty_like(ids)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fl.flash_knn_graph(params, dev, k, ids, cnt, stream)
+
+    ms = _timed(step, 3)
+    ph = _phases(fl, step, 2)
+    plain_ms = _timed(lambda: fl.flash_knn_graph_plain(params, dev, k, ids, cnt, stream), 1)
+    plain_ph = _phases(fl, lambda: fl.flash_knn_graph_plain(params, dev, k, ids, cnt, stream), 1)
+    torch.cuda.synchronize()
+    hashes = torch.empty((n, p.K * p.L), dtype=torch.int32, device="cuda")
+    hash_ms = _timed(lambda: fl.flash_hash(params, dev, hashes, stream), 3)
+    del hashes
+    keys = fl.row_keys(params, dev)
+    keys_ms = _timed(lambda: fl.flash_keys(params, dev, keys, stream), 3)
+    ix = fl.flash_build(params, dev)
+    m_total = _candidates(fl, ix, keys, p.R)
+    ix.free()
+    del keys, ids, cnt, dev
+    torch.cuda.empty_cache()
+    peak, src = _peak()
+    T = 1 << p.range_bits
+    b_keys = 8 * (n + 1) + 4 * nnz + 4 * p.L * n
+    b_hash = 8 * (n + 1) + 4 * nnz + 4 * p.K * p.L * n
+    b_sort = 4 * p.L * n + 4 * p.L * n + 4 * p.L * (T + 1)
+    b_query = 4 * p.L * n + 4 * m_total + 8 * k * n
+
+    def roof(bytes_, ms_):
+        return {"algorithmic_bytes": bytes_, "duration_ms": ms_, "achieved_GB/s": bytes_ / (ms_ / 1e3) / 1e9,
+                "frac": bytes_ / (ms_ / 1e3) / 1e9 / peak}
+
+    return {"workload": w.name, "n_rows": n, "nnz": nnz, "graph_ms": ms, "queries_per_s": n / (ms / 1e3),
+            "phases_ms": ph, "plain_graph_ms": plain_ms, "plain_queries_per_s": n / (plain_ms / 1e3),
+            "plain_phases_ms": plain_ph, "speedup_vs_plain": plain_ms / ms,
+            "candidates_per_query": m_total / n, "peak_GB/s": peak, "peak_source": src,
+            "rooflines": {
+                "hash_phase (keys, 8(N+1)+4nnz+4LN)": roof(b_keys, ph.get("hash", keys_ms)),
+                "sort+reservoir (4LN keys read + 4LN ids + 4L(T+1) starts written)":
+                    roof(b_sort, ph.get("sort", 0.0) + ph.get("reservoir", 0.0)),
+                "query (sum_t (4 + 4 min(m_t,R)) + 8k per query)": roof(b_query, ph.get("query", ms))},
+            "flash_hash": {"ms": hash_ms, "bytes": b_hash, "bytes_formula": "8(N+1) + 4 nnz + 4 K L N",
+                           "GB/s": b_hash / (hash_ms / 1e3) / 1e9, "frac": b_hash / (hash_ms / 1e3) / 1e9 / peak},
+            "flash_keys": {"ms": keys_ms, "bytes": b_keys, "bytes_formula": "8(N+1) + 4 nnz + 4 L N",
+                           "GB/s": b_keys / (keys_ms / 1e3) / 1e9, "frac": b_keys / (keys_ms / 1e3) / 1e9 / peak}}
+
+
+def pinned_copy_ceiling(nbytes: int = 4 << 30) -> dict:
+    """Host->device and device->host bandwidth of one large copy from / to pinned memory (the ceiling
+    of the end-to-end number, whose inputs cross the host link every step)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h2d = _timed(lambda: d.copy_(h, non_blocking=True), 3)
+    d2h = _timed(lambda: h.copy_(d, non_blocking=True), 3)
+    del h, d
+    torch.cuda.empty_cache()
+    return {"bytes": nbytes, "h2d_GB/s": nbytes / (h2d / 1e3) / 1e9, "d2h_GB/s": nbytes / (d2h / 1e3) / 1e9}
 
 
 def run_reference(args):
@@ -409,56 +584,37 @@ def main():
     value = world * n / (ms / 1000.0)
 
     # per-phase device times (same kernels, same launches; events on the stream between phases)
-    fl.flash_enable_phase_timing(True)
-    acc = {}
-    for _ in range(args.steps):
-        step()
-        for name, v in fl.flash_phase_times().items():
-            acc[name] = acc.get(name, 0.0) + v / args.steps
-    fl.flash_enable_phase_timing(False)
+    acc = _phases(fl, step, args.steps)
 
     # DOPH kernels timed alone: the keys epilogue (the graph's hash phase) and the hashes output (DOPH GB/s)
     keys_out = torch.empty((p.L, n), dtype=torch.int32, device="cuda")
     hashes_out = torch.empty((n, p.K * p.L), dtype=torch.int32, device="cuda")
 
-    def timed(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
     graph_ms = None
     try:
         from paper_1709_01190_gb300 import tuning as _t
         g = _t.GraphedKnnGraph(params, dev, k, ids, cnt)
-        graph_ms = timed(g.replay, max(args.steps, 5))
+        graph_ms = _timed(g.replay, max(args.steps, 5), stream)
         del g
     except Exception as e:  # report, do not fail the bench
         graph_ms = f"capture failed: {e}"
 
-    keys_ms = timed(lambda: fl.flash_keys(params, dev, keys_out, stream), max(args.steps, 5))
-    hash_ms = timed(lambda: fl.flash_hash(params, dev, hashes_out, stream), max(args.steps, 5))
+    keys_ms = _timed(lambda: fl.flash_keys(params, dev, keys_out, stream), max(args.steps, 5), stream)
+    hash_ms = _timed(lambda: fl.flash_hash(params, dev, hashes_out, stream), max(args.steps, 5), stream)
     in_bytes = 8 * (n + 1) + 4 * nnz
-    keys_bytes = in_bytes + 4 * p.L * n           # flash_keys: one key array
-    phase_bytes = in_bytes + 8 * p.L * n          # graph hash phase: keys table-major + row-major copy
+    keys_bytes = in_bytes + 4 * p.L * n           # the fused keys path: one key array
     hash_bytes = in_bytes + 4 * p.K * p.L * n
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs")
-    peak, peak_src = (hbm, "measured") if hbm else (6800.0, "fallback")
+    peak, peak_src = _peak()
     hash_phase_ms = acc.get("hash", keys_ms)
-    achieved = phase_bytes / (hash_phase_ms / 1000.0) / 1e9
+    achieved = keys_bytes / (hash_phase_ms / 1000.0) / 1e9
     roofline = {"kernel": "doph_kernel<keys> (hash phase of the graph step)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, torch copy read+write; kernel timed "
-                                          "inside the step, burst copy figure)",
-                "algorithmic_bytes_per_launch": phase_bytes,
-                "bytes_formula": "8(N+1) + 4 nnz + 8 L N", "traffic": None,
-                "duration_ms": hash_phase_ms}
+                "peak_source": peak_src + " (torch copy read+write; kernel timed inside the step, burst copy figure)",
+                "algorithmic_bytes_per_launch": keys_bytes,
+                "bytes_formula": "8(N+1) + 4 nnz + 4 L N (the fused keys path)",
+                "overhead_bytes_per_launch": 4 * p.L * n,
+                "overhead": "a row-major copy of the keys for the graph's queries (4 L N written), not counted",
+                "traffic": None, "duration_ms": hash_phase_ms}
     prof = os.path.join(ROOT, "profiles", "doph_keys_webspam_like_traffic.json")
     if os.path.exists(prof) and not args.rows and args.workload == "webspam_like":
         try:
@@ -473,7 +629,17 @@ def main():
             pass
     doph = {"GB/s": hash_bytes / (hash_ms / 1000.0) / 1e9, "ms": hash_ms, "bytes": hash_bytes,
             "frac_of_hbm_peak": hash_bytes / (hash_ms / 1000.0) / 1e9 / peak,
-            "bytes_formula": "8(N+1) + 4 nnz + 4 K L N", "keys_epilogue_GB/s": keys_bytes / (keys_ms / 1e3) / 1e9}
+            "bytes_formula": "8(N+1) + 4 nnz + 4 K L N", "keys_epilogue_GB/s": keys_bytes / (keys_ms / 1e3) / 1e9,
+            "keys_frac_of_hbm_peak": keys_bytes / (keys_ms / 1e3) / 1e9 / peak}
+
+    # the plain, unbatched GPU path on the same rows (same results; a baseline)
+    plain = None
+    if world == 1:
+        plain_ms = _timed(lambda: fl.flash_knn_graph_plain(params, dev, k, ids, cnt, stream), 2, stream)
+        plain = {"api": "flash_knn_graph_plain", "ms_per_step": plain_ms, "value": n / (plain_ms / 1e3),
+                 "unit": "queries/s", "phases_ms": _phases(
+                     fl, lambda: fl.flash_knn_graph_plain(params, dev, k, ids, cnt, stream), 1),
+                 "speedup_of_optimised": plain_ms / ms}
 
     # the two densifications (rotation; optimal, [36]) on sparse kdd12-like rows, where most bins are empty
     densify = None
@@ -487,7 +653,7 @@ def main():
         dms = {}
         for mode in (0, 1):
             pm = fl.FlashParams(pk.K, pk.L, pk.R, pk.range_bits, pk.seed, densify=mode)
-            dms[mode] = timed(lambda: fl.flash_keys(pm, dk, kout, stream), 3)
+            dms[mode] = _timed(lambda: fl.flash_keys(pm, dk, kout, stream), 3, stream)
         densify = {"workload": f"kdd12-like rows: {ck.n_rows:,} rows, {ck.nnz:,} non-zeros, K={pk.K} L={pk.L} "
                                f"(B={pk.K * pk.L}), flash_keys",
                    "rotation_ms": dms[0], "optimal_ms": dms[1],
@@ -508,15 +674,23 @@ def main():
             tt = torch.tensor([e2e_s], device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_s = float(tt.item())
+        link = pinned_copy_ceiling()
         e2e = {"value": world * n / e2e_s, "unit": "queries/s", "ms_per_step": e2e_s * 1000.0,
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * n * k,
-               "api": "flash_knn_graph_host (pinned host buffers)"}
+               "api": "flash_knn_graph_host (pinned host buffers)",
+               "link_ceiling": {**link, "ms_per_step_at_ceiling":
+                                1e3 * (in_bytes / (link["h2d_GB/s"] * 1e9) + 8 * n * k / (link["d2h_GB/s"] * 1e9)),
+                                "frac": (1e3 * (in_bytes / (link["h2d_GB/s"] * 1e9) +
+                                                8 * n * k / (link["d2h_GB/s"] * 1e9))) / (e2e_s * 1000.0)}}
 
-    served = None
-    if rank == 0 and world == 1 and not args.no_serve and not args.rows:
+    config3 = served = config4 = None
+    if rank == 0 and world == 1 and not args.rows:
         del dev, keys_out, hashes_out
         torch.cuda.empty_cache()
-        served = serving_measurement(fl)
+        if not args.no_url:
+            config3, served = url_section(fl, args, tune=not args.no_tune)
+        if not args.no_kdd12:
+            config4 = kdd12_section(fl, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -528,8 +702,9 @@ def main():
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded, webspam-shaped; see config)",
                 "config": config_of(w, csr), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "phases_ms": acc, "doph": doph, "densify": densify, "graph_replay_ms_per_step": graph_ms,
-                "tuning": tuned,
+                "phases_ms": acc, "doph": doph, "plain": plain, "densify": densify,
+                "graph_replay_ms_per_step": graph_ms, "tuning": tuned,
+                "config3_url_like_batch": config3, "config4_kdd12_like_graph": config4,
                 "served": served, "reduced": bool(args.rows)}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -44,7 +44,7 @@ enum {
   FLASH_EINVAL = 1,   /* invalid or unsupported argument (host-side check) */
   FLASH_ENOMEM = 2,   /* device allocation failed or scratch budget exceeded */
   FLASH_ECUDA = 3,    /* a CUDA runtime call failed */
-  FLASH_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  FLASH_ETIMEOUT = 4, /* reserved: no kernel of this version waits on another, so none is returned */
   FLASH_EDATA = 5     /* invalid input found on the device (see flash_device_error) */
 };
 
@@ -52,7 +52,7 @@ enum {
 enum {
   FLASH_DEVERR_COL_RANGE = 1u, /* a column id outside [0, dim) was skipped */
   FLASH_DEVERR_ROW_PTR = 2u,   /* a row with end < start or end > nnz was treated as empty */
-  FLASH_DEVERR_TIMEOUT = 4u    /* a bounded spin-wait expired */
+  FLASH_DEVERR_TIMEOUT = 4u    /* reserved: never raised (no kernel of this version spin-waits) */
 };
 
 /* Method parameters (Section 2.2: K hashes per meta-hash, L tables;
@@ -163,6 +163,17 @@ int flash_query_noalloc(const flash_index *index, const flash_csr *q, int32_t k,
 int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_t *out_ids, int32_t *out_counts,
                     void *stream);
 
+/* The plain, unbatched GPU path: the same all-points k-NN graph as
+ * flash_knn_graph (bit-identical results), computed the straightforward way as
+ * a baseline -- one block per row for the hashes, one stable library radix
+ * sort for the grouping, Algorithm 1 one thread per bucket, and the query as
+ * the paper's own GPU design (Section 3.4.1): gather, segmented sort, count
+ * runs, segmented sort by (count, id), first k -- one launch per stage, in
+ * chunks of queries.  Needs L * (2^range_bits + 1) <= 2^32.
+ *   out_ids, out_counts : DEVICE int32 [n_rows][k] */
+int flash_knn_graph_plain(const flash_params *p, const flash_csr *x, int32_t k, int32_t *out_ids,
+                          int32_t *out_counts, void *stream);
+
 /* Same as flash_knn_graph with every buffer in HOST memory: the call brings
  * the CSR to the device, runs the graph and copies the results back, then
  * synchronizes `stream`.  Inputs in pinned memory (allocated or registered
@@ -218,10 +229,12 @@ typedef struct flash_tuning {
 int flash_set_tuning(const flash_tuning *t);
 int flash_get_tuning(flash_tuning *t);
 
-/* Per-phase device timing of the calling thread's flash_knn_graph calls
- * (instrumentation; off by default).  flash_enable_phase_timing(1) makes
- * later calls record a CUDA event on their stream before each phase (hash,
- * sort, reservoir, query) and at the end; it returns the previous setting.
+/* Per-phase device timing of the calling thread's flash_knn_graph,
+ * flash_knn_graph_plain and flash_query calls (instrumentation; off by
+ * default).  flash_enable_phase_timing(1) makes later calls record a CUDA
+ * event on their stream before each phase (hash, sort, reservoir, query; the
+ * plain path: hash, group, query) and at the end; it returns the previous
+ * setting.
  * flash_phase_times() waits for the last call's final event and writes up to
  * max_phases durations in milliseconds (ms) and phase names (names, static
  * strings; may be NULL); it returns the number written (0 when disabled). */
@@ -229,8 +242,8 @@ int flash_enable_phase_timing(int on);
 int flash_phase_times(float *ms, const char **names, int max_phases);
 
 /* Number of CUDA kernels the calling thread's last flash_hash, flash_keys,
- * flash_build, flash_query or flash_knn_graph call launched (memsets of
- * scratch counters are not kernels and are not counted). */
+ * flash_build, flash_query, flash_query_noalloc or flash_knn_graph call
+ * launched (memsets of scratch counters are not kernels and are not counted). */
 int flash_last_launch_count(void);
 
 /* Human-readable text for a status code. */

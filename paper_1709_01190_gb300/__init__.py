@@ -21,7 +21,8 @@ from .build import build as _build_lib
 
 __all__ = [
     "FlashError", "FlashParams", "DeviceCSR", "FlashIndex", "build",
-    "flash_hash", "flash_keys", "flash_build", "flash_query", "flash_knn_graph", "flash_knn_graph_host",
+    "flash_hash", "flash_keys", "flash_build", "flash_query", "flash_knn_graph", "flash_knn_graph_plain",
+    "flash_knn_graph_host",
     "flash_index_export", "flash_device_error", "flash_set_scratch_budget", "flash_knn_graph_scratch_bytes",
     "flash_query_scratch_bytes", "flash_strerror", "flash_version",
     "hash_rows", "row_keys", "knn_graph", "DEVERR_COL_RANGE", "DEVERR_ROW_PTR", "DEVERR_TIMEOUT",
@@ -188,6 +189,15 @@ def flash_knn_graph(params: FlashParams, x: DeviceCSR, k: int, out_ids, out_coun
                                 _stream(stream)), "flash_knn_graph")
 
 
+def flash_knn_graph_plain(params: FlashParams, x: DeviceCSR, k: int, out_ids, out_counts, stream=None) -> None:
+    """The plain, unbatched GPU path (a baseline): the same graph as flash_knn_graph."""
+    _check_out(out_ids, (x.n_rows, k), "int32")
+    _check_out(out_counts, (x.n_rows, k), "int32")
+    p, c = params.c(), x.c()
+    check(lib().flash_knn_graph_plain(ctypes.byref(p), ctypes.byref(c), int(k), _ptr(out_ids), _ptr(out_counts),
+                                      _stream(stream)), "flash_knn_graph_plain")
+
+
 def flash_knn_graph_host(params: FlashParams, row_ptr, col, dim: int, k: int, out_ids, out_counts,
                          stream=None) -> None:
     """Host-buffer variant: numpy (ideally pinned) inputs and outputs; synchronizes the stream."""
@@ -271,6 +281,14 @@ def knn_graph(params: FlashParams, x: DeviceCSR, k: int, stream=None):
     ids = torch.empty((x.n_rows, k), dtype=torch.int32, device="cuda")
     cnt = torch.empty((x.n_rows, k), dtype=torch.int32, device="cuda")
     flash_knn_graph(params, x, k, ids, cnt, stream)
+    return ids, cnt
+
+
+def knn_graph_plain(params: FlashParams, x: DeviceCSR, k: int, stream=None):
+    import torch
+    ids = torch.empty((x.n_rows, k), dtype=torch.int32, device="cuda")
+    cnt = torch.empty((x.n_rows, k), dtype=torch.int32, device="cuda")
+    flash_knn_graph_plain(params, x, k, ids, cnt, stream)
     return ids, cnt
 
 

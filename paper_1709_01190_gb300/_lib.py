@@ -57,6 +57,7 @@ def lib():
             "flash_query": ([VP, C, I32, VP, VP, VP, VP], ctypes.c_int),
             "flash_knn_graph": ([P, C, I32, VP, VP, VP], ctypes.c_int),
             "flash_query_noalloc": ([VP, C, I32, VP, VP, VP, VP], ctypes.c_int),
+            "flash_knn_graph_plain": ([P, C, I32, VP, VP, VP], ctypes.c_int),
             "flash_knn_graph_host": ([P, VP, VP, I64, I64, I32, VP, VP, VP], ctypes.c_int),
             "flash_index_free": ([VP], None),
             "flash_index_get_info": ([VP, ctypes.POINTER(IndexInfo)], ctypes.c_int),

@@ -444,13 +444,18 @@ int flash_query(const flash_index *ix, const flash_csr *q, int32_t k, const int3
   ar.add(&overflow, nq);
   ro.plan(ar, tu, nq);
   if (int rc = ar.alloc(st)) return rc;
+  g_timer.begin();
+  g_timer.mark("hash", st);
   DophLaunch dl = doph_args(p, ix->s, q, true, nullptr, nq, counters + 3, tu);
   dl.out_rowmajor = qkeys;
   if (int rc = ro.apply(dl, q, st)) return rc;
   if (int rc = launch_doph(dl, st)) return rc;
-  return launch_query(query_args(p, qkeys, true, nq, nq, ix->ids, ix->starts, ix->n, k, exclude_ids, false, out_ids,
-                                 out_counts, counters, overflow),
-                      st);
+  g_timer.mark("query", st);
+  const int rc = launch_query(query_args(p, qkeys, true, nq, nq, ix->ids, ix->starts, ix->n, k, exclude_ids, false,
+                                         out_ids, out_counts, counters, overflow),
+                              st);
+  g_timer.mark("end", st);
+  return rc;
 }
 
 int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_t *out_ids, int32_t *out_counts,
@@ -481,6 +486,77 @@ int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_
   const int rc = launch_query(query_args(p, b.keys_rm, true, n, n, ids, starts, n, k, nullptr, true, out_ids,
                                          out_counts, b.counters + 4, overflow),
                               st);
+  g_timer.mark("end", st);
+  return rc;
+}
+
+// The plain, unbatched path: the same graph, one launch (or one library sort)
+// per stage, no persistent claims, no row order, no tuned knobs.
+int flash_knn_graph_plain(const flash_params *p, const flash_csr *x, int32_t k, int32_t *out_ids,
+                          int32_t *out_counts, void *stream) {
+  if (int rc = check_params(p)) return rc;
+  if (int rc = check_csr(x)) return rc;
+  if (k < 1 || k > 1024) return FLASH_EINVAL;
+  reset_launch_count();
+  if (x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
+  // the sort keys t * (2^rb + 1) + address must fit 32 bits
+  if (static_cast<uint64_t>(p->L) * ((1ull << p->range_bits) + 1) > 0xFFFFFFFFull) return FLASH_EINVAL;
+  if (x->n_rows > 0 && (!out_ids || !out_counts)) return FLASH_EINVAL;
+  if (x->n_rows == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = x->n_rows, ln = static_cast<int64_t>(p->L) * n;
+  const Seeds s = derive_seeds(p->seed);
+  const int64_t chunk = plain_query_chunk(p->L, p->R, n);
+  const int64_t lr = static_cast<int64_t>(p->L) * p->R;
+  Arena ar;
+  uint32_t *comp = nullptr, *comp2 = nullptr, *keys_rm = nullptr, *starts = nullptr, *cand = nullptr, *cand2 = nullptr;
+  int32_t *ids_in = nullptr, *ids = nullptr;
+  int64_t *seg_b = nullptr, *seg_e = nullptr;
+  void *temp = nullptr;
+  const size_t sort_tb = plain_sort_temp_bytes(n, p->L, p->range_bits);
+  const size_t seg_tb = plain_segsort_temp_bytes(chunk, p->L, p->R);
+  const size_t tb = sort_tb > seg_tb ? sort_tb : seg_tb;
+  ar.add(&comp, ln);
+  ar.add(&comp2, ln);
+  ar.add(&keys_rm, ln);
+  ar.add(&ids_in, ln);
+  ar.add(&ids, ln);
+  ar.add(&starts, static_cast<int64_t>(p->L) * ((1LL << p->range_bits) + 1));
+  ar.add(&cand, chunk * lr);
+  ar.add(&cand2, chunk * lr);
+  ar.add(&seg_b, chunk);
+  ar.add(&seg_e, chunk);
+  ar.add(reinterpret_cast<char **>(&temp), static_cast<int64_t>(tb));
+  if (int rc = ar.alloc(st)) return rc;
+  g_timer.begin();
+  g_timer.mark("hash", st);
+  PlainHashLaunch h{x->row_ptr, x->col, n, x->nnz, x->dim, p->K * p->L, p->K, p->L, p->range_bits, p->densify, s,
+                    comp, keys_rm, device_error_word()};
+  if (int rc = launch_plain_keys(h, st)) return rc;
+  g_timer.mark("group", st);
+  PlainGroupLaunch g{comp, comp2, ids_in, ids, starts, n, p->L, p->R, p->range_bits, s.r, temp, tb};
+  if (int rc = launch_plain_group(g, st)) return rc;
+  g_timer.mark("query", st);
+  PlainQueryLaunch q{};
+  q.keys_rm = keys_rm;
+  q.ids = ids;
+  q.starts = starts;
+  q.n = n;
+  q.L = p->L;
+  q.R = p->R;
+  q.range_bits = p->range_bits;
+  q.k = k;
+  q.exclude = nullptr;
+  q.exclude_self = true;
+  q.out_ids = out_ids;
+  q.out_counts = out_counts;
+  q.cand = cand;
+  q.cand2 = cand2;
+  q.seg_begin = seg_b;
+  q.seg_end = seg_e;
+  q.temp = temp;
+  q.temp_bytes = tb;
+  const int rc = launch_plain_query(q, n, st);
   g_timer.mark("end", st);
   return rc;
 }
@@ -592,13 +668,16 @@ size_t flash_knn_graph_scratch_bytes(const flash_params *p, int64_t n_rows) {
 
 size_t flash_query_scratch_bytes(const flash_params *p, int64_t q_rows) {
   if (check_hash_params(p) || q_rows < 0) return 0;
+  // the same carve as flash_query, under the current tuning (the row order adds its scratch)
   Arena ar;
   uint32_t *qkeys = nullptr;
   unsigned long long *counters = nullptr;
   int64_t *overflow = nullptr;
+  RowOrder ro;
   ar.add(&qkeys, static_cast<int64_t>(p->L) * q_rows);
   ar.add(&counters, 8);
   ar.add(&overflow, q_rows);
+  ro.plan(ar, current_tuning(), q_rows);
   return ar.bytes();
 }
 

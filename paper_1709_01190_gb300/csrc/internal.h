@@ -118,6 +118,54 @@ struct QueryLaunch {
 };
 int launch_query(const QueryLaunch &l, cudaStream_t stream);
 
+// ---- the plain, unbatched path (a baseline; plain.cu)
+struct PlainHashLaunch {
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int64_t n_rows, nnz, dim;
+  uint32_t B, K, L, range_bits, densify;
+  Seeds seeds;
+  uint32_t *comp;     // [L][n_rows]: t * (2^rb + 1) + address (the sort keys)
+  uint32_t *keys_rm;  // [n_rows][L]: addresses (the queries' keys)
+  uint32_t *err;
+};
+int launch_plain_keys(const PlainHashLaunch &a, cudaStream_t stream);
+
+struct PlainGroupLaunch {
+  const uint32_t *comp_in;  // [L][n]
+  uint32_t *comp_out;       // [L][n]
+  int32_t *ids_in;          // [L][n] scratch (the values: point ids)
+  int32_t *ids_out;         // [L][n] the index's grouped ids
+  uint32_t *starts;         // [L][2^rb + 1]
+  int64_t n;
+  uint32_t L, R, range_bits;
+  uint64_t rkey;            // reservoir key (Seeds::r)
+  void *temp;
+  size_t temp_bytes;
+};
+size_t plain_sort_temp_bytes(int64_t n, uint32_t L, uint32_t range_bits);
+int launch_plain_group(const PlainGroupLaunch &g, cudaStream_t stream);
+
+struct PlainQueryLaunch {
+  const uint32_t *keys_rm;  // [nq][L]
+  const int32_t *ids;       // index [L][n]
+  const uint32_t *starts;   // index [L][2^rb + 1]
+  int64_t n;
+  uint32_t L, R, range_bits;
+  int32_t k;
+  const int32_t *exclude;
+  bool exclude_self;
+  int32_t *out_ids, *out_counts;
+  uint32_t *cand, *cand2;   // [chunk][L*R] each
+  const uint32_t *sorted;   // set by the launcher
+  int64_t *seg_begin, *seg_end;  // [chunk]
+  void *temp;
+  size_t temp_bytes;
+};
+int64_t plain_query_chunk(uint32_t L, uint32_t R, int64_t nq);
+size_t plain_segsort_temp_bytes(int64_t chunk, uint32_t L, uint32_t R);
+int launch_plain_query(const PlainQueryLaunch &a, int64_t nq, cudaStream_t stream);
+
 // ---- dense export of the tables
 int launch_export(const int32_t *ids, const uint32_t *starts, int64_t n, uint32_t L, uint32_t R, uint32_t range_bits,
                   int32_t *tables, uint32_t *counts, cudaStream_t stream);

@@ -72,6 +72,7 @@ extern "C" int flash_query_noalloc(const flash_index *ix, const flash_csr *q, in
     return FLASH_EINVAL;
   if ((reinterpret_cast<uintptr_t>(q->row_ptr) & 7u) || (reinterpret_cast<uintptr_t>(q->col) & 3u)) return FLASH_EINVAL;
   if (q->n_rows > 0 && (!out_ids || !out_counts)) return FLASH_EINVAL;
+  reset_launch_count();
   if (q->n_rows == 0) return 0;
   const flash_params *p = &ix->p;
   const int64_t nq = q->n_rows;

@@ -281,24 +281,26 @@ class CudaBackend:
         self._bufs = [None] * self.n_slots
 
     def batch_bytes(self, rows: int, nnz: int) -> int:
-        return 8 * (rows + 1) + 4 * nnz + 8 * rows * self.k + self._scratch(rows)
+        """Device bytes one batch holds while in flight: its CSR, its results (each rounded to the
+        caching allocator's 512-byte blocks) and the library's scratch for it."""
+        def blk(nb):
+            return (nb + 511) // 512 * 512
+        return (blk(8 * (rows + 1)) + blk(4 * max(nnz, 1)) + 2 * blk(4 * rows * self.k) +
+                self._scratch(rows))
 
-    def _buffers(self, slot: int, rows: int, nnz: int):
+    def _host_buffers(self, slot: int, rows: int, nnz: int):
+        """Pinned host staging of a slot, grown to the largest batch the slot has seen (host memory
+        only: the device buffers of a batch live exactly as long as the batch, see launch)."""
         torch = self.torch
         b = self._bufs[slot]
         if b is None or b["rows"] < rows or b["nnz"] < nnz:
             R = max(rows, b["rows"] if b else 0, 256)
             Z = max(nnz, b["nnz"] if b else 0, 4096)
-            with torch.cuda.stream(self.streams[slot]):
-                b = {"rows": R, "nnz": Z,
-                     "h_rp": torch.empty(R + 1, dtype=torch.int64, pin_memory=True),
-                     "h_col": torch.empty(Z, dtype=torch.int32, pin_memory=True),
-                     "h_ids": torch.empty(R * self.k, dtype=torch.int32, pin_memory=True),
-                     "h_cnt": torch.empty(R * self.k, dtype=torch.int32, pin_memory=True),
-                     "d_rp": torch.empty(R + 1, dtype=torch.int64, device=self.device),
-                     "d_col": torch.empty(Z, dtype=torch.int32, device=self.device),
-                     "d_ids": torch.empty(R * self.k, dtype=torch.int32, device=self.device),
-                     "d_cnt": torch.empty(R * self.k, dtype=torch.int32, device=self.device)}
+            b = {"rows": R, "nnz": Z,
+                 "h_rp": torch.empty(R + 1, dtype=torch.int64, pin_memory=True),
+                 "h_col": torch.empty(Z, dtype=torch.int32, pin_memory=True),
+                 "h_ids": torch.empty(R * self.k, dtype=torch.int32, pin_memory=True),
+                 "h_cnt": torch.empty(R * self.k, dtype=torch.int32, pin_memory=True)}
             self._bufs[slot] = b
         return b
 
@@ -307,24 +309,29 @@ class CudaBackend:
         from . import DeviceCSR, flash_query
         rp, col = concat_requests(batch.requests)
         rows, nnz = batch.rows, int(rp[-1])
-        b = self._buffers(slot, rows, nnz)
+        b = self._host_buffers(slot, rows, nnz)
         s = self.streams[slot]
         b["h_rp"][:rows + 1].numpy()[:] = rp
         if nnz:
             b["h_col"][:nnz].numpy()[:] = col
         with torch.cuda.stream(s):
-            b["d_rp"][:rows + 1].copy_(b["h_rp"][:rows + 1], non_blocking=True)
+            # device buffers sized for this batch (the bytes batch_bytes admitted); they are
+            # released when the batch completes, so device memory held by the server is exactly
+            # that of the batches in flight (torch's caching allocator reuses the blocks)
+            d_rp = torch.empty(rows + 1, dtype=torch.int64, device=self.device)
+            d_col = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
+            d_ids = torch.empty((rows, self.k), dtype=torch.int32, device=self.device)
+            d_cnt = torch.empty((rows, self.k), dtype=torch.int32, device=self.device)
+            d_rp.copy_(b["h_rp"][:rows + 1], non_blocking=True)
             if nnz:
-                b["d_col"][:nnz].copy_(b["h_col"][:nnz], non_blocking=True)
-            x = DeviceCSR(b["d_rp"][:rows + 1], b["d_col"][:max(nnz, 1)], self.dim, nnz=nnz)
-            ids = b["d_ids"][:rows * self.k].view(rows, self.k)
-            cnt = b["d_cnt"][:rows * self.k].view(rows, self.k)
-            flash_query(self.index, x, self.k, None, ids, cnt, s)
-            b["h_ids"][:rows * self.k].copy_(b["d_ids"][:rows * self.k], non_blocking=True)
-            b["h_cnt"][:rows * self.k].copy_(b["d_cnt"][:rows * self.k], non_blocking=True)
+                d_col[:nnz].copy_(b["h_col"][:nnz], non_blocking=True)
+            x = DeviceCSR(d_rp, d_col, self.dim, nnz=nnz)
+            flash_query(self.index, x, self.k, None, d_ids, d_cnt, s)
+            b["h_ids"][:rows * self.k].copy_(d_ids.view(-1), non_blocking=True)
+            b["h_cnt"][:rows * self.k].copy_(d_cnt.view(-1), non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        return {"ev": ev, "slot": slot, "rows": rows}
+        return {"ev": ev, "slot": slot, "rows": rows, "dev": (d_rp, d_col, d_ids, d_cnt)}
 
     def poll(self, h) -> bool:
         return h["ev"].query()
@@ -333,6 +340,8 @@ class CudaBackend:
         h["ev"].synchronize()
 
     def results(self, h):
+        h["ev"].synchronize()
+        h["dev"] = None  # the batch is complete: its device buffers go back to the allocator
         b = self._bufs[h["slot"]]
         rows = h["rows"]
         ids = b["h_ids"][:rows * self.k].numpy().reshape(rows, self.k)

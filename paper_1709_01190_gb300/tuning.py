@@ -173,3 +173,29 @@ class GraphedKnnGraph:
     def replay(self):
         self.graph.replay()
         return self.ids, self.counts
+
+
+class GraphedQuery:
+    """One flash_query call over a fixed batch of query rows captured as a CUDA graph (DOPH of the
+    rows -> gather -> count -> top-k, with the call's stream-ordered scratch).  Replays read the
+    batch from, and write the results to, the same device buffers; replays must not overlap."""
+
+    def __init__(self, index, q, k: int, exclude_ids=None, out_ids=None, out_counts=None):
+        import torch
+        from . import flash_device_error, flash_query
+        self.ids = out_ids if out_ids is not None else torch.empty((q.n_rows, k), dtype=torch.int32, device="cuda")
+        self.counts = out_counts if out_counts is not None else torch.empty_like(self.ids)
+        flash_device_error()  # the device error word is allocated before any capture
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            flash_query(index, q, k, exclude_ids, self.ids, self.counts, side)  # warm-up outside the graph
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            flash_query(index, q, k, exclude_ids, self.ids, self.counts, torch.cuda.current_stream())
+
+    def replay(self):
+        self.graph.replay()
+        return self.ids, self.counts

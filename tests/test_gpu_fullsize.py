@@ -109,11 +109,27 @@ def test_url_like_index_and_batched_queries_full_size():
     for s0, sz in zip(starts, sizes):
         part = qc.slice(s0, s0 + sz)
         tickets.append((s0, sz, srv.submit(part.row_ptr, part.col)))
+    served_i, served_c, served_rows = [], [], []
     for s0, sz, t in tickets:
         si, sc = t.wait(120)
         assert np.array_equal(si, ids[s0:s0 + sz]) and np.array_equal(sc, cnt[s0:s0 + sz])
+        served_i.append(si)
+        served_c.append(sc)
+        served_rows.append(np.arange(s0, s0 + sz))
     srv.close()
     ix.free()
+    # rows the served requests carried, checked one by one against the oracle (Algorithm 3 on the
+    # buckets rebuilt from their arrival streams): a few from every request, 320 in all
+    served_i = np.concatenate(served_i)
+    served_c = np.concatenate(served_c)
+    served_rows = np.concatenate(served_rows)
+    rng = np.random.default_rng(21)
+    first_rows = np.flatnonzero(np.isin(served_rows, starts))  # the first row of every request
+    pick = np.unique(np.concatenate([first_rows, rng.choice(len(served_rows), 320, replace=False)]))
+    sub = qc.rows(served_rows[pick])
+    qk = oracle.keys(sub.row_ptr, sub.col, p.K, p.L, p.range_bits, p.seed)
+    _check_queries(keys_all, c.row_ptr, p, qk, np.diff(sub.row_ptr) == 0, w.k, served_i[pick], served_c[pick],
+                   np.full(len(pick), -1, np.int32))
 
 
 def test_kdd12_like_graph_full_size():

@@ -389,3 +389,77 @@ def test_bad_columns_and_row_pointers_raise_the_device_flag():
     h = fl.hash_rows(p, x2)
     assert fl.flash_device_error() & fl.DEVERR_ROW_PTR
     assert np.all(u32(h)[1:] == 0xFFFFFFFF)  # rows 1 and 2 treated as empty
+
+
+def test_scratch_budget_below_need_returns_enomem_and_nothing_is_launched():
+    """Host-side allocation-failure injection: a scratch budget below what a call needs makes
+    flash_knn_graph and flash_query fail with FLASH_ENOMEM before any launch; the library stays
+    usable, and the same calls succeed (and match the oracle) once the budget is restored."""
+    w = synth.WORKLOADS["tiny_plain"].scaled(2_000)
+    c = synth.generate(w.data)
+    p = params_of(w)
+    dev = fl.DeviceCSR.from_host(c)
+    need_graph = fl.flash_knn_graph_scratch_bytes(p, c.n_rows)
+    need_query = fl.flash_query_scratch_bytes(p, c.n_rows)
+    assert need_graph > 0 and need_query > 0
+    ix = fl.flash_build(p, dev)
+    ids = torch.full((c.n_rows, w.k), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.full_like(ids, -7)
+    old = fl.flash_set_scratch_budget(need_graph - 1)
+    try:
+        with pytest.raises(fl.FlashError) as e:
+            fl.flash_knn_graph(p, dev, w.k, ids, cnt)
+        assert e.value.code == 2  # FLASH_ENOMEM
+        assert fl.flash_last_launch_count() == 0
+        fl.flash_set_scratch_budget(need_query - 1)
+        with pytest.raises(fl.FlashError) as e:
+            fl.flash_query(ix, dev, w.k, None, ids, cnt)
+        assert e.value.code == 2
+        assert fl.flash_last_launch_count() == 0
+        torch.cuda.synchronize()
+        assert int((ids != -7).sum()) == 0  # nothing was written
+        fl.flash_set_scratch_budget(need_query)  # exactly enough
+        fl.flash_query(ix, dev, w.k, torch.arange(c.n_rows, dtype=torch.int32, device="cuda"), ids, cnt)
+    finally:
+        fl.flash_set_scratch_budget(old)
+    ei, en = oracle.knn_graph(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, w.k)
+    assert np.array_equal(ids.cpu().numpy(), ei) and np.array_equal(cnt.cpu().numpy(), en)
+    gi, gc = fl.knn_graph(p, dev, w.k)
+    assert np.array_equal(gi.cpu().numpy(), ei) and np.array_equal(gc.cpu().numpy(), en)
+    ix.free()
+
+
+# ------------------------------------------------ the plain, unbatched path
+
+PLAIN_CASES = [
+    ("tiny_plain", 10_000, None, 0),
+    ("tiny_plain", 2_500, dict(range_bits=3, R=1), 0),       # every bucket heavy, R = 1
+    ("tiny_plain", 4_000, dict(range_bits=5, R=8), 1),       # optimal densification
+    ("webspam_like", 2_000, dict(range_bits=12), 0),
+    ("url_like_batched", 12_000, dict(range_bits=11), 0),    # thousands of candidates per query
+    ("kdd12_like", 25_000, dict(range_bits=13), 0),          # B = 1024, most bins densified
+]
+
+
+@pytest.mark.parametrize("name,n,over,densify", PLAIN_CASES)
+def test_knn_graph_plain_path(name, n, over, densify):
+    """flash_knn_graph_plain (the baseline) gives the oracle's graph, element by element."""
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p0 = _params_override(w, over)
+    p = fl.FlashParams(p0.K, p0.L, p0.R, p0.range_bits, p0.seed, densify=densify)
+    ids, cnt = fl.knn_graph_plain(p, fl.DeviceCSR.from_host(c), w.k)
+    ei, en = oracle.knn_graph(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, w.k, densify=densify)
+    assert fl.flash_device_error() == 0
+    assert np.array_equal(ids.cpu().numpy(), ei)
+    assert np.array_equal(cnt.cpu().numpy(), en)
+
+
+def test_knn_graph_plain_path_with_empty_rows_and_edge_columns():
+    rng = np.random.default_rng(12)
+    dim = 5000
+    c = csr_of(adversarial_rows(rng, 24, dim, n=1500), dim)
+    p = fl.FlashParams(3, 8, 5, 5, 77)
+    ids, cnt = fl.knn_graph_plain(p, fl.DeviceCSR.from_host(c), 7)
+    ei, en = oracle.knn_graph(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, 7)
+    assert np.array_equal(ids.cpu().numpy(), ei) and np.array_equal(cnt.cpu().numpy(), en)

@@ -100,3 +100,25 @@ def test_noalloc_query_keeps_the_index_densification():
                           w.k, densify=1)
     assert np.array_equal(got[0].cpu().numpy(), ei) and np.array_equal(got[1].cpu().numpy(), en)
     ix.free()
+
+
+def test_noalloc_query_needs_no_scratch_budget(index_and_queries):
+    """The entry point allocates nothing: under a one-byte scratch budget it still runs and
+    matches flash_query, while flash_query itself (which allocates its scratch) is refused."""
+    ix, qa, _, k = index_and_queries
+    exp = fl.query(ix, qa, k)
+    torch.cuda.synchronize()
+    old = lib().flash_set_scratch_budget(1)
+    try:
+        got = _noalloc(ix, qa, k)  # asserts a zero status
+        ids = torch.empty((qa.n_rows, k), dtype=torch.int32, device="cuda")
+        cnt = torch.empty_like(ids)
+        c = qa.c()
+        rc = lib().flash_query(ix.handle, ctypes.byref(c), k, None, ctypes.c_void_p(ids.data_ptr()),
+                               ctypes.c_void_p(cnt.data_ptr()),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == 2  # FLASH_ENOMEM: flash_query's scratch does not fit the budget
+    finally:
+        lib().flash_set_scratch_budget(old)
+    assert torch.equal(got[0], exp[0]) and torch.equal(got[1], exp[1])
+    assert lib().flash_last_launch_count() == 0  # the refused call launched nothing
