@@ -128,6 +128,17 @@ int flash_keys(const flash_params *p, const flash_csr *x, uint32_t *keys, void *
  * The index is complete when the work queued on `stream` completes. */
 int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, void *stream);
 
+/* ADD continued (Algorithm 2 is a stream): index the rows of x as new points
+ * with ids index->n_rows, index->n_rows + 1, ... .  In every bucket the new
+ * points continue the arrival ranks from the bucket's stored count, so the
+ * tables afterwards equal those of one flash_build over the old and the new
+ * rows together (bit for bit, with the same seed).  The index's tables are
+ * replaced by larger ones; the call synchronizes `stream` before it frees the
+ * old ones and returns.  FLASH_EINVAL when the index would exceed 2^24 - 2
+ * points or belongs to another device than the current one.  On error the
+ * index is unchanged. */
+int flash_add(flash_index *index, const flash_csr *x, void *stream);
+
 /* Querying phase (Algorithm 3): for every row of q, gather its L buckets,
  * count how often each id occurs and report the k most frequent, ties broken
  * by smaller id.  Missing entries are (-1, 0).  A row with no entries
@@ -242,7 +253,7 @@ int flash_enable_phase_timing(int on);
 int flash_phase_times(float *ms, const char **names, int max_phases);
 
 /* Number of CUDA kernels the calling thread's last flash_hash, flash_keys,
- * flash_build, flash_query, flash_query_noalloc or flash_knn_graph call
+ * flash_build, flash_add, flash_query, flash_query_noalloc or flash_knn_graph call
  * launched (memsets of scratch counters are not kernels and are not counted). */
 int flash_last_launch_count(void);
 

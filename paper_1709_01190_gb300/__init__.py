@@ -21,7 +21,7 @@ from .build import build as _build_lib
 
 __all__ = [
     "FlashError", "FlashParams", "DeviceCSR", "FlashIndex", "build",
-    "flash_hash", "flash_keys", "flash_build", "flash_query", "flash_knn_graph", "flash_knn_graph_plain",
+    "flash_hash", "flash_keys", "flash_build", "flash_add", "flash_query", "flash_knn_graph", "flash_knn_graph_plain",
     "flash_knn_graph_host",
     "flash_index_export", "flash_device_error", "flash_set_scratch_budget", "flash_knn_graph_scratch_bytes",
     "flash_query_scratch_bytes", "flash_strerror", "flash_version",
@@ -171,6 +171,13 @@ def flash_build(params: FlashParams, x: DeviceCSR, stream=None) -> FlashIndex:
     h = ctypes.c_void_p(0)
     check(lib().flash_build(ctypes.byref(p), ctypes.byref(c), ctypes.byref(h), _stream(stream)), "flash_build")
     return FlashIndex(h.value, params, x.n_rows)
+
+
+def flash_add(index: FlashIndex, x: DeviceCSR, stream=None) -> None:
+    """Index the rows of x as new points index.n_rows, index.n_rows + 1, ... (Algorithm 2 continued)."""
+    c = x.c()
+    check(lib().flash_add(index.handle, ctypes.byref(c), _stream(stream)), "flash_add")
+    index.n_rows += x.n_rows
 
 
 def flash_query(index: FlashIndex, q: DeviceCSR, k: int, exclude_ids, out_ids, out_counts, stream=None) -> None:

@@ -55,6 +55,7 @@ def lib():
             "flash_keys": ([P, C, VP, VP], ctypes.c_int),
             "flash_build": ([P, C, ctypes.POINTER(VP), VP], ctypes.c_int),
             "flash_query": ([VP, C, I32, VP, VP, VP, VP], ctypes.c_int),
+            "flash_add": ([VP, C, VP], ctypes.c_int),
             "flash_knn_graph": ([P, C, I32, VP, VP, VP], ctypes.c_int),
             "flash_query_noalloc": ([VP, C, I32, VP, VP, VP, VP], ctypes.c_int),
             "flash_knn_graph_plain": ([P, C, I32, VP, VP, VP], ctypes.c_int),

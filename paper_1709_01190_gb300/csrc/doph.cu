@@ -47,6 +47,7 @@ struct DophParams {
   uint32_t B, K, L, rb, W, G;  // W = bitmap words, G = summary words
   uint32_t densify;            // 0 rotation, 1 optimal densification
   uint32_t rows_per_grab;
+  uint32_t bin_words;  // W * 33 rounded up to a multiple of 4 (room for either layout)
   uint32_t smem_words_per_warp;
   Seeds s;
   uint32_t *out;      // hashes [n][B], or keys [L][ld] (may be null in keys mode)
@@ -57,6 +58,15 @@ struct DophParams {
   unsigned long long *row_counter;
   const int32_t *order;  // optional processing order of the rows (longest first)
 };
+
+// Shared-memory position of bin j.  Sparse rows keep one pad word after every
+// 32 bins, so that lane l walking bins 32 l .. 32 l + 31 (the densification)
+// and lanes reading consecutive bins both hit 32 different banks; dense rows
+// keep the bins unpadded (their insertion loop is the kernel's hot loop).
+template <bool PAD>
+__device__ __forceinline__ uint32_t bix(uint32_t j) {
+  return PAD ? j + (j >> 5) : j;
+}
 
 __device__ __forceinline__ void bin_and_offset(uint32_t c, const Seeds &s, uint32_t B, uint32_t &bin,
                                                uint32_t &off) {
@@ -180,10 +190,10 @@ __device__ __forceinline__ void sparse_row(const DophParams &a, int64_t start, i
     uint32_t bin = 0, off = 0;
     if (valid) bin_and_offset(c, a.s, a.B, bin, off);
     const uint32_t bit = 1u << (bin & 31);
-    if (valid && !(mask[bin >> 5] & bit)) bins[bin] = 0xFFFFFFFFu;
+    if (valid && !(mask[bin >> 5] & bit)) bins[bix<true>(bin)] = 0xFFFFFFFFu;
     __syncwarp();
     if (valid) {
-      atomicMin(&bins[bin], off);
+      atomicMin(&bins[bix<true>(bin)], off);
       atomicOr(&mask[bin >> 5], bit);
     }
     __syncwarp();
@@ -204,24 +214,31 @@ __device__ __forceinline__ void dense_mask(const DophParams &a, const uint32_t *
 }
 
 // The emit of row r from its B final bins: the L keys or the B hashes.
-template <bool KEYS>
+template <bool KEYS, bool PAD>
 __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const uint32_t *bins, uint32_t lane) {
   const uint32_t B = a.B;
   if (KEYS) {
     const int sh = 64 - static_cast<int>(a.rb);
     for (uint32_t t = lane; t < a.L; t += 32) {
       uint64_t x = 0;
-      for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[t + i * a.L];
+      for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[bix<PAD>(t + i * a.L)];
       const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
       if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
       if (a.out_rm) a.out_rm[r * a.L + t] = key;
     }
-  } else if (a.vec_out) {
+  } else if (a.vec_out && !PAD) {
     uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
     const uint4 *src = reinterpret_cast<const uint4 *>(bins);
     for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) __stcs(o + q4, src[q4]);
+  } else if (a.vec_out) {
+    uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
+    for (uint32_t q4 = lane; q4 < B / 4; q4 += 32) {
+      const uint32_t j = 4 * q4;
+      __stcs(o + q4, make_uint4(bins[bix<true>(j)], bins[bix<true>(j + 1)], bins[bix<true>(j + 2)],
+                                bins[bix<true>(j + 3)]));
+    }
   } else {
-    for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[j];
+    for (uint32_t j = lane; j < B; j += 32) a.out[r * B + j] = bins[bix<PAD>(j)];
   }
   __syncwarp();
 }
@@ -235,6 +252,7 @@ __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const u
 // non-empty ones read.
 __device__ __forceinline__ bool bin_filled(const uint32_t *mask, uint32_t b) { return (mask[b >> 5] >> (b & 31)) & 1u; }
 
+template <bool PAD>
 __device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mask, uint32_t B, uint64_t d,
                                              uint32_t lane) {
   const uint32_t imax = 8u * B;  // a multiple of 4
@@ -266,13 +284,13 @@ __device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mas
         }
       }
     }
-    bins[j] = bins[src];
+    bins[bix<PAD>(j)] = bins[bix<PAD>(src)];
   }
   __syncwarp();
 }
 
 // Densification by rotation and the emit of row r (keys or hashes).
-template <bool KEYS>
+template <bool KEYS, bool PAD>
 __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint32_t *bins, const uint32_t *mask,
                                            uint32_t lane) {
   const uint32_t B = a.B, W = a.W;
@@ -292,7 +310,35 @@ __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint3
     return;
   }
   if (filled < B && a.densify) {
-    optimal_densify(bins, mask, a.B, a.s.d, lane);
+    optimal_densify<PAD>(bins, mask, a.B, a.s.d, lane);
+  } else if (filled < B && PAD) {
+    // lane l walks its words l, l + 32, ... from the top bit down, carrying the
+    // nearest filled bin to the right (the first one of the next non-empty word
+    // at the start, B further when that is a wrap-around); an empty bin j gets
+    // v[src] + (src - j) * C.  With the padded layout, the 32 lanes' bins
+    // 32 l + b lie in 32 different banks.  Only empty bins are written and
+    // only filled ones read.
+    for (uint32_t w = lane; w < W; w += 32) {
+      const uint32_t m = mask[w];
+      if (m == 0xFFFFFFFFu) continue;
+      const int w2 = next_word_circular(sw, a.G, w + 1 < W ? w + 1 : 0);
+      const uint32_t m2 = mask[w2];
+      const uint32_t s2 = 32u * static_cast<uint32_t>(w2) + (__ffs(m2) - 1);
+      uint32_t cur = s2 + (static_cast<uint32_t>(w2) <= w ? B : 0u);  // wrapped: distance counts B
+      uint32_t curv = bins[bix<true>(s2)];
+      const uint32_t j0 = 32u * w;
+#pragma unroll
+      for (int b = 31; b >= 0; --b) {
+        const uint32_t j = j0 + b;
+        if ((m >> b) & 1u) {
+          cur = j;
+          curv = bins[bix<true>(j)];
+        } else {
+          bins[bix<true>(j)] = curv + (cur - j) * kRotStep;  // bins past B (last word) are never read
+        }
+      }
+    }
+    __syncwarp();
   } else if (filled < B) {
     // word by word, lane l takes bin 32w + l: the words and the next non-empty
     // word are warp-uniform (broadcast reads), bins are consecutive per lane
@@ -314,7 +360,7 @@ __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint3
     }
     __syncwarp();
   }
-  emit_row<KEYS>(a, r, bins, lane);
+  emit_row<KEYS, PAD>(a, r, bins, lane);
 }
 
 // The 16-byte aligned body [a4, a4 + 4 nq) of the row [start, end), from the
@@ -334,7 +380,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
   uint32_t *bins = smem + warp * a.smem_words_per_warp;
-  uint32_t *mask = bins + a.W * 32;
+  uint32_t *mask = bins + a.bin_words;
   const uint32_t B = a.B, W = a.W;
   const uint32_t a1_lo = static_cast<uint32_t>(a.s.a1), a1_hi = static_cast<uint32_t>(a.s.a1 >> 32);
   const uint64_t b1 = a.s.b1;
@@ -372,11 +418,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
 
     if (n <= static_cast<int64_t>(B / 2)) {
       sparse_row(a, start, end, bins, mask, lane);
-      finish_row<KEYS>(a, r, bins, mask, lane);
+      finish_row<KEYS, true>(a, r, bins, mask, lane);
     } else if (B & 1u) {  // odd B: element by element
       insert_row_checked(a, start, end, bins, mask, lane);
       dense_mask(a, bins, mask, lane);
-      finish_row<KEYS>(a, r, bins, mask, lane);
+      finish_row<KEYS, false>(a, r, bins, mask, lane);
     } else {
       // ---- dense row: head up to a 16-byte boundary, 16-byte body in groups
       // of 128 int4 (4 per lane), the last group partial, tail; the columns
@@ -449,9 +495,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
       if (__any_sync(kFull, empty_bin)) {
         for (uint32_t w = lane; w < W; w += 32) mask[w] = 0;
         dense_mask(a, bins, mask, lane);
-        finish_row<KEYS>(a, r, bins, mask, lane);
+        finish_row<KEYS, false>(a, r, bins, mask, lane);
       } else {
-        emit_row<KEYS>(a, r, bins, lane);
+        emit_row<KEYS, false>(a, r, bins, lane);
       }
     }
   }
@@ -546,7 +592,8 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.rb = L.range_bits;
   a.W = (a.B + 31) / 32;
   a.G = (a.W + 31) / 32;
-  a.smem_words_per_warp = a.W * 32 + ((a.W + 3) & ~3u);
+  a.bin_words = (a.W * 33 + 3) & ~3u;
+  a.smem_words_per_warp = a.bin_words + ((a.W + 3) & ~3u);
   a.s = L.seeds;
   a.densify = L.densify;
   a.out = L.out;

@@ -251,9 +251,10 @@ void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, in
   ar.add(&b.counters, 8);
 }
 
-// K1 (keys) -> K2 -> K3 into (ids, starts)
+// K1 (keys) -> K2 -> K3 into (ids, starts); without K3 when reservoir is false
+// (a batch that continues an index: its draws follow the stored counts)
 int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildScratch &b, int32_t *ids,
-              uint32_t *starts, cudaStream_t st) {
+              uint32_t *starts, cudaStream_t st, bool reservoir = true) {
   const int64_t n = x->n_rows;
   g_timer.mark("hash", st);
   DophLaunch dl = doph_args(p, s, x, true, b.transpose ? nullptr : b.keys, n, b.counters, b.tu);
@@ -282,6 +283,7 @@ int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildSc
   sl.heavy = b.heavy;
   sl.heavy_cap = b.heavy_cap;
   if ((rc = sort_tables(b.plan, sl, st))) return rc;
+  if (!reservoir) return 0;
   g_timer.mark("reservoir", st);
   ReservoirLaunch rl{};
   rl.ids = ids;
@@ -367,15 +369,22 @@ int flash_keys(const flash_params *p, const flash_csr *x, uint32_t *keys, void *
   if (x->n_rows == 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const flash_tuning tu = current_tuning();
+  // short rows (fewer non-zeros than tables): row-major keys first, then a tiled
+  // transpose (the table-major keys of short rows are scattered 4-byte stores)
+  const bool transpose = x->nnz < static_cast<int64_t>(p->L) * x->n_rows;
   Arena ar;
   unsigned long long *counter = nullptr;
+  uint32_t *rm = nullptr;
   RowOrder ro;
   ar.add(&counter, 1);
+  if (transpose) ar.add(&rm, static_cast<int64_t>(p->L) * x->n_rows);
   ro.plan(ar, tu, x->n_rows);
   if (int rc = ar.alloc(st)) return rc;
-  DophLaunch dl = doph_args(p, derive_seeds(p->seed), x, true, keys, x->n_rows, counter, tu);
+  DophLaunch dl = doph_args(p, derive_seeds(p->seed), x, true, transpose ? nullptr : keys, x->n_rows, counter, tu);
+  dl.out_rowmajor = rm;
   if (int rc = ro.apply(dl, x, st)) return rc;
-  return launch_doph(dl, st);
+  if (int rc = launch_doph(dl, st)) return rc;
+  return transpose ? launch_transpose_keys(rm, x->n_rows, p->L, keys, x->n_rows, st) : 0;
 }
 
 int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, void *stream) {
@@ -420,6 +429,82 @@ int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, vo
     return rc;
   }
   *out = ix;
+  return 0;
+}
+
+int flash_add(flash_index *ix, const flash_csr *x, void *stream) {
+  reset_launch_count();
+  if (!ix) return FLASH_EINVAL;
+  if (int rc = check_csr(x)) return rc;
+  if (x->n_rows == 0) return 0;
+  if (ix->n + x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const flash_params *p = &ix->p;
+  const int64_t n_old = ix->n, n_new = x->n_rows, n = n_old + n_new;
+  const int64_t T1 = (1LL << p->range_bits) + 1;
+  int cur_dev = 0;
+  cudaGetDevice(&cur_dev);
+  if (cur_dev != ix->device) return FLASH_EINVAL;
+  int32_t *ids = nullptr;
+  uint32_t *starts = nullptr;
+  const size_t ids_b = sizeof(int32_t) * static_cast<size_t>(p->L) * static_cast<size_t>(n);
+  const size_t st_b = sizeof(uint32_t) * static_cast<size_t>(p->L) * static_cast<size_t>(T1);
+  if (cudaMalloc(&ids, ids_b) != cudaSuccess || cudaMalloc(&starts, st_b) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ids);
+    cudaFree(starts);
+    return FLASH_ENOMEM;
+  }
+  int rc = 0;
+  {
+    Arena ar;
+    BuildScratch b;
+    plan_build(ar, b, p, n_new, x->nnz);
+    int32_t *bids = nullptr;
+    uint32_t *bstarts = nullptr;
+    uint64_t *heavy = nullptr;
+    unsigned long long *hcount = nullptr;
+    const int64_t cap = reservoir_heavy_capacity(n, p->L, p->R, p->range_bits);
+    ar.add(&bids, static_cast<int64_t>(p->L) * n_new);
+    ar.add(&bstarts, static_cast<int64_t>(p->L) * T1);
+    ar.add(&heavy, cap);
+    ar.add(&hcount, 1);
+    rc = ar.alloc(st);
+    if (!rc) rc = run_build(p, ix->s, x, b, bids, bstarts, st, false);
+    if (!rc) {
+      AddLaunch a{};
+      a.old_ids = ix->ids;
+      a.old_starts = ix->starts;
+      a.n_old = n_old;
+      a.new_ids = bids;
+      a.new_starts = bstarts;
+      a.n_new = n_new;
+      a.ids = ids;
+      a.starts = starts;
+      a.id0 = static_cast<int32_t>(n_old);
+      a.L = p->L;
+      a.R = p->R;
+      a.range_bits = p->range_bits;
+      a.rkey = ix->s.r;
+      a.heavy_count = hcount;
+      a.heavy = heavy;
+      a.heavy_cap = cap;
+      rc = launch_add(a, st);
+    }
+  }
+  // the old tables are read by the work just queued: wait for it before freeing them
+  const int rs = cuda_ok(cudaStreamSynchronize(st));
+  if (rc || rs) {
+    cudaFree(ids);
+    cudaFree(starts);
+    return rc ? rc : rs;
+  }
+  cudaFree(ix->ids);
+  cudaFree(ix->starts);
+  ix->ids = ids;
+  ix->starts = starts;
+  ix->n = n;
+  ix->bytes = static_cast<int64_t>(ids_b + st_b);
   return 0;
 }
 

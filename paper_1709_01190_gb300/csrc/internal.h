@@ -166,6 +166,25 @@ int64_t plain_query_chunk(uint32_t L, uint32_t R, int64_t nq);
 size_t plain_segsort_temp_bytes(int64_t chunk, uint32_t L, uint32_t R);
 int launch_plain_query(const PlainQueryLaunch &a, int64_t nq, cudaStream_t stream);
 
+// ---- ADD continued on an existing index (add.cu)
+struct AddLaunch {
+  const int32_t *old_ids;      // [L][n_old], the index's grouped ids
+  const uint32_t *old_starts;  // [L][2^rb + 1]
+  int64_t n_old;
+  const int32_t *new_ids;      // [L][n_new], the batch grouped by the same sort (ids 0 .. n_new - 1)
+  const uint32_t *new_starts;  // [L][2^rb + 1]
+  int64_t n_new;
+  int32_t *ids;                // [L][n_old + n_new], merged
+  uint32_t *starts;            // [L][2^rb + 1], merged
+  int32_t id0;                 // id of the batch's first point (n_old)
+  uint32_t L, R, range_bits;
+  uint64_t rkey;               // reservoir key (Seeds::r)
+  unsigned long long *heavy_count;  // 8 bytes of scratch
+  uint64_t *heavy;             // buckets with draws, capacity heavy_cap
+  int64_t heavy_cap;
+};
+int launch_add(const AddLaunch &a, cudaStream_t stream);
+
 // ---- dense export of the tables
 int launch_export(const int32_t *ids, const uint32_t *starts, int64_t n, uint32_t L, uint32_t R, uint32_t range_bits,
                   int32_t *tables, uint32_t *counts, cudaStream_t stream);

@@ -463,3 +463,67 @@ def test_knn_graph_plain_path_with_empty_rows_and_edge_columns():
     ids, cnt = fl.knn_graph_plain(p, fl.DeviceCSR.from_host(c), 7)
     ei, en = oracle.knn_graph(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, 7)
     assert np.array_equal(ids.cpu().numpy(), ei) and np.array_equal(cnt.cpu().numpy(), en)
+
+
+# ------------------------------------------ ADD continued (Algorithm 2 as a stream)
+
+ADD_CASES = [
+    ("tiny_plain", 6_000, dict(range_bits=6, R=3), [2_000, 1_500, 2_500]),   # every bucket overflows
+    ("tiny_plain", 4_000, dict(range_bits=3, R=1), [1, 3_000, 999]),        # R = 1, one-row batch
+    ("tiny_plain", 5_000, None, [4_000, 1_000]),
+    ("url_like_batched", 16_000, dict(range_bits=12), [9_000, 7_000]),       # Zipf heavy buckets, R = 128
+    ("kdd12_like", 20_000, dict(range_bits=13, L=32), [12_000, 8_000]),
+    ("webspam_like", 3_000, dict(range_bits=10, L=8), [1_000, 2_000]),
+]
+
+
+@pytest.mark.parametrize("name,n,over,parts", ADD_CASES)
+def test_add_continues_every_bucket_like_one_build(name, n, over, parts):
+    """flash_build on the first rows, then flash_add of the rest in batches: the tables equal the
+    oracle's build over all rows slot for slot (counts included), and queries agree with the oracle."""
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = _params_override(w, over)
+    assert sum(parts) == c.n_rows
+    r0 = parts[0]
+    ix = fl.flash_build(p, fl.DeviceCSR.from_host(c.slice(0, r0)))
+    for sz in parts[1:]:
+        fl.flash_add(ix, fl.DeviceCSR.from_host(c.slice(r0, r0 + sz)))
+        r0 += sz
+    assert ix.n_rows == c.n_rows and ix.info()["n_rows"] == c.n_rows
+    tables, counts = ix.export()
+    et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
+    assert np.array_equal(u32(counts).reshape(ec.shape), ec)
+    assert np.array_equal(tables.cpu().numpy(), et)
+    # the same tables through the oracle's own ADD on the same batches
+    ot, oc = oracle.build_tables(c.row_ptr[:parts[0] + 1], c.col[:int(c.row_ptr[parts[0]])], p.K, p.L, p.R,
+                                 p.range_bits, p.seed)
+    r0 = parts[0]
+    for sz in parts[1:]:
+        sub = c.slice(r0, r0 + sz)
+        oracle.add_rows(ot, oc, sub.row_ptr, sub.col, r0, p.K, p.L, p.R, p.range_bits, p.seed)
+        r0 += sz
+    assert np.array_equal(ot, et) and np.array_equal(oc, ec)
+    qids = synth.sample_rows(c.n_rows, min(300, c.n_rows), seed=9)
+    sub = c.rows(qids)
+    ids, cnt = fl.query(ix, fl.DeviceCSR.from_host(sub), w.k, torch.from_numpy(qids.astype(np.int32)).cuda())
+    ei, en = oracle.query(et, ec, p.K, p.L, p.R, p.range_bits, p.seed, sub.row_ptr, sub.col, w.k,
+                          exclude=qids.astype(np.int32))
+    assert np.array_equal(ids.cpu().numpy(), ei) and np.array_equal(cnt.cpu().numpy(), en)
+    assert fl.flash_device_error() == 0
+    ix.free()
+
+
+def test_add_rows_with_empty_rows_and_an_empty_batch():
+    rng = np.random.default_rng(21)
+    dim = 3000
+    c = csr_of(adversarial_rows(rng, 15, dim, n=1200), dim)
+    p = fl.FlashParams(3, 5, 2, 4, 99)
+    ix = fl.flash_build(p, fl.DeviceCSR.from_host(c.slice(0, 500)))
+    fl.flash_add(ix, fl.DeviceCSR.from_host(c.slice(500, 500)))  # no rows: nothing changes
+    fl.flash_add(ix, fl.DeviceCSR.from_host(c.slice(500, 1200)))
+    tables, counts = ix.export()
+    et, ec = oracle.build_tables(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed)
+    assert np.array_equal(u32(counts).reshape(ec.shape), ec)
+    assert np.array_equal(tables.cpu().numpy(), et)
+    ix.free()
