@@ -61,6 +61,13 @@ def _lib():
         lib.oracle_address.argtypes = [_P, _U32, _U32, _U32, _U32, _U64]
         lib.oracle_build_tables_from_keys.argtypes = [_P, _I64, _P, _I64, _U32, _U32, _U32, _U32, _U64, _P, _P]
         lib.oracle_address.restype = ctypes.c_uint32
+        lib.oracle_pool_index.argtypes = [_U32, _U32, _U32, _U64]
+        lib.oracle_pool_index.restype = ctypes.c_uint32
+        lib.oracle_build_shared.argtypes = [_P, _P, _I64, _U32, _U32, _U32, _U32, _U64, _U32, _U32, _P, _P]
+        lib.oracle_build_shared.restype = ctypes.c_int
+        lib.oracle_query_shared.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _U64, _U32, _U32, _P, _P, _I64, _I32,
+                                            _P, _P, _P]
+        lib.oracle_query_shared.restype = ctypes.c_int
         for f in ("oracle_hash", "oracle_keys", "oracle_build", "oracle_bucket", "oracle_kselect",
                   "oracle_query", "oracle_query_one_streamed", "oracle_knn_graph", "oracle_build_tables_from_keys"):
             getattr(lib, f).restype = ctypes.c_int
@@ -282,3 +289,50 @@ def _pmap(fn, items):
         return
     with ThreadPoolExecutor(max_workers=_workers(None)) as ex:
         list(ex.map(fn, items))
+
+
+# ------------------------------------------------ reservoir sharing (Section 3.5)
+
+def pool_index(t: int, b: int, P: int, seed: int) -> int:
+    """The reservoir of the shared pool that bucket b of table t points to."""
+    return int(_lib().oracle_pool_index(t, b, P, seed))
+
+
+def build_tables_shared(row_ptr, col, K, L, R, range_bits, seed, P, densify=0):
+    """Adding phase with reservoir sharing: (tables int32 [P][R], counts uint32 [P])."""
+    rp, prp = _c(row_ptr, np.int64)
+    cl, pcl = _c(col, np.int32)
+    n = rp.shape[0] - 1
+    tables = np.empty((P, R), dtype=np.int32)
+    counts = np.empty(P, dtype=np.uint32)
+    _check(_lib().oracle_build_shared(prp, pcl if cl.size else None, n, K, L, R, range_bits, seed, densify, P,
+                                      tables.ctypes.data, counts.ctypes.data))
+    return tables, counts
+
+
+def query_shared(tables, counts, K, L, R, range_bits, seed, P, q_row_ptr, q_col, k, exclude=None, densify=0):
+    """Querying phase with reservoir sharing.  Returns (ids int32 [nq][k], counts int32 [nq][k])."""
+    tb, ptb = _c(tables, np.int32)
+    ct, pct = _c(counts, np.uint32)
+    rp, prp = _c(q_row_ptr, np.int64)
+    cl, pcl = _c(q_col, np.int32)
+    nq = rp.shape[0] - 1
+    ids = np.empty((nq, k), dtype=np.int32)
+    cnt = np.empty((nq, k), dtype=np.int32)
+    ex = None
+    if exclude is not None:
+        ex, pex = _c(exclude, np.int32)
+    _check(_lib().oracle_query_shared(ptb, pct, K, L, R, range_bits, seed, densify, P, prp,
+                                      pcl if cl.size else None, nq, k, None if ex is None else pex,
+                                      ids.ctypes.data, cnt.ctypes.data))
+    return ids, cnt
+
+
+def knn_graph_shared(row_ptr, col, K, L, R, range_bits, seed, k, P, densify=0):
+    """All-points k-NN graph over an index with reservoir sharing."""
+    rp, _ = _c(row_ptr, np.int64)
+    cl, _ = _c(col, np.int32)
+    n = rp.shape[0] - 1
+    tables, counts = build_tables_shared(rp, cl, K, L, R, range_bits, seed, P, densify)
+    return query_shared(tables, counts, K, L, R, range_bits, seed, P, rp, cl, k,
+                        exclude=np.arange(n, dtype=np.int32), densify=densify)

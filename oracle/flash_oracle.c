@@ -33,9 +33,10 @@
  *   a1, b1 : the permutation surrogate pi (one-permutation hashing)
  *   a2, b2 : MapKHashesToAddress
  *   r      : key of the reservoir random numbers (Algorithm 1 / 2)
- *   d      : key of the probe sequence of optimal densification            */
+ *   d      : key of the probe sequence of optimal densification
+ *   e      : key of the bucket -> reservoir map of reservoir sharing       */
 typedef struct {
-  uint64_t a1, b1, a2, b2, r, d;
+  uint64_t a1, b1, a2, b2, r, d, e;
 } oracle_seeds_t;
 
 static uint64_t splitmix64_next(uint64_t *state) {
@@ -63,6 +64,7 @@ static oracle_seeds_t make_seeds(uint64_t seed) {
   s.b2 = splitmix64_next(&st);
   s.r = splitmix64_next(&st);
   s.d = splitmix64_next(&st);
+  s.e = splitmix64_next(&st);
   return s;
 }
 
@@ -484,4 +486,107 @@ int oracle_knn_graph(const int64_t *row_ptr, const int32_t *col, int64_t n, uint
 uint32_t oracle_address(const uint32_t *h, uint32_t t, uint32_t K, uint32_t L, uint32_t rb, uint64_t seed) {
   oracle_seeds_t s = make_seeds(seed);
   return map_k_hashes_to_address(h, t, K, L, rb, &s);
+}
+
+
+/* ------------------------------------------- reservoir sharing (Section 3.5)
+ * Section 3.2 (item 4), Section 3.5 and Figure 3: instead of one reservoir per
+ * bucket, one shared pool of P reservoirs (Allocated Range = F * Actual
+ * Range, over all L tables: P = F * L * 2^rb) serves every table; a bucket
+ * points to a randomly chosen reservoir of the pool.  Readings:
+ *   - the pointer of bucket b of table t is a fixed random map
+ *       pool(t, b) = ((mix(e XOR (t * 2^32 + b)) >> 32) * P) >> 32,
+ *     mix = the SplitMix64 output function, e the seventh SplitMix64 output
+ *     of the seed (the paper assigns pool reservoirs at first use; a fixed
+ *     map gives the same distribution and keeps the Adding phase
+ *     data-parallel);
+ *   - a shared reservoir receives its arrivals in the order of Algorithm 2's
+ *     loop: points in id order, and for each point the tables in order;
+ *   - its random numbers are keyed by (seed, 2^32 - 1, reservoir, arrival
+ *     rank), the draw of Algorithms 1 and 2 for a "table" 2^32 - 1 no real
+ *     table uses;
+ *   - Querying (Algorithm 3) gathers, for every table t, the reservoir its
+ *     bucket points to (a reservoir two buckets of the query share is
+ *     gathered twice).                                                     */
+static uint32_t pool_index(const oracle_seeds_t *s, uint32_t t, uint32_t b, uint32_t P) {
+  uint64_t u = splitmix64_mix(s->e ^ (((uint64_t)t << 32) + (uint64_t)b));
+  return (uint32_t)(((u >> 32) * (uint64_t)P) >> 32);
+}
+
+uint32_t oracle_pool_index(uint32_t t, uint32_t b, uint32_t P, uint64_t seed) {
+  oracle_seeds_t s = make_seeds(seed);
+  return pool_index(&s, t, b, P);
+}
+
+/* Adding phase with reservoir sharing: tables[x * R + slot], counts[x] for
+ * the P reservoirs of the pool.                                            */
+int oracle_build_shared(const int64_t *row_ptr, const int32_t *col, int64_t n, uint32_t K, uint32_t L, uint32_t R,
+                        uint32_t rb, uint64_t seed, uint32_t densify, uint32_t P, int32_t *tables, uint32_t *counts) {
+  uint32_t B = K * L, t;
+  oracle_seeds_t s = make_seeds(seed);
+  uint32_t *all_hashes = (uint32_t *)malloc(sizeof(uint32_t) * B);
+  uint32_t *v = (uint32_t *)malloc(sizeof(uint32_t) * B);
+  uint8_t *filled = (uint8_t *)malloc(B);
+  uint32_t *nx = (uint32_t *)malloc(sizeof(uint32_t) * B);
+  int64_t p;
+  uint64_t z;
+  if (!all_hashes || !v || !filled || !nx) { free(all_hashes); free(v); free(filled); free(nx); return -1; }
+  for (z = 0; z < (uint64_t)P * R; ++z) tables[z] = -1;
+  memset(counts, 0, sizeof(uint32_t) * (size_t)P);
+  for (p = 0; p < n; ++p) {                                   /* for each DataPoint */
+    int64_t nnz = row_ptr[p + 1] - row_ptr[p];
+    if (nnz == 0) continue;
+    doph_row(col + row_ptr[p], nnz, B, &s, densify, all_hashes, v, filled, nx);
+    for (t = 0; t < L; ++t) {                                 /* for each Table_t */
+      uint32_t key = map_k_hashes_to_address(all_hashes, t, K, L, rb, &s);
+      uint32_t x = pool_index(&s, t, key, P);                 /* the shared reservoir it points to */
+      add(tables + (uint64_t)x * R, counts + x, R, s.r, 0xFFFFFFFFu, x, (int32_t)p);
+    }
+  }
+  free(all_hashes);
+  free(v);
+  free(filled);
+  free(nx);
+  return 0;
+}
+
+/* Querying phase with reservoir sharing, against tables from
+ * oracle_build_shared.                                                     */
+int oracle_query_shared(const int32_t *tables, const uint32_t *counts, uint32_t K, uint32_t L, uint32_t R,
+                        uint32_t rb, uint64_t seed, uint32_t densify, uint32_t P, const int64_t *q_row_ptr,
+                        const int32_t *q_col, int64_t nq, int32_t k, const int32_t *exclude, int32_t *out_ids,
+                        int32_t *out_counts) {
+  uint32_t B = K * L, t;
+  oracle_seeds_t s = make_seeds(seed);
+  uint32_t *all_hashes = (uint32_t *)malloc(sizeof(uint32_t) * B);
+  uint32_t *v = (uint32_t *)malloc(sizeof(uint32_t) * B);
+  uint8_t *filled = (uint8_t *)malloc(B);
+  uint32_t *nx = (uint32_t *)malloc(sizeof(uint32_t) * B);
+  int32_t *A = (int32_t *)malloc(sizeof(int32_t) * (size_t)L * R);
+  int64_t q;
+  if (!all_hashes || !v || !filled || !nx || !A) {
+    free(all_hashes); free(v); free(filled); free(nx); free(A);
+    return -1;
+  }
+  for (q = 0; q < nq; ++q) {
+    int64_t nnz = q_row_ptr[q + 1] - q_row_ptr[q], na = 0;
+    int32_t e;
+    if (nnz == 0) {
+      for (e = 0; e < k; ++e) { out_ids[q * k + e] = -1; out_counts[q * k + e] = 0; }
+      continue;
+    }
+    doph_row(q_col + q_row_ptr[q], nnz, B, &s, densify, all_hashes, v, filled, nx);
+    for (t = 0; t < L; ++t) {
+      uint32_t key = map_k_hashes_to_address(all_hashes, t, K, L, rb, &s);
+      uint32_t x = pool_index(&s, t, key, P), m = counts[x] < R ? counts[x] : R, j;
+      for (j = 0; j < m; ++j) A[na++] = tables[(uint64_t)x * R + j];
+    }
+    oracle_kselect(A, na, exclude ? exclude[q] : -1, k, out_ids + q * k, out_counts + q * k);
+  }
+  free(all_hashes);
+  free(v);
+  free(filled);
+  free(nx);
+  free(A);
+  return 0;
 }

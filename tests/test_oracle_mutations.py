@@ -66,6 +66,13 @@ MUTATIONS = {
     "optimal_probe_ignores_attempt": ("splitmix64_mix(s->d ^ (((uint64_t)j << 32) | i))",
                                       "splitmix64_mix(s->d ^ (((uint64_t)j << 32) | 1))",
                                       "test_optimal_densification_picks_sources_independently_per_bin"),
+    "pool_ignores_table": ("splitmix64_mix(s->e ^ (((uint64_t)t << 32) + (uint64_t)b))",
+                           "splitmix64_mix(s->e ^ ((uint64_t)b))",
+                           "test_shared_pool_map_is_uniform_and_independent_across_tables"),
+    "shared_build_wrong_reservoir": ("uint32_t x = pool_index(&s, t, key, P);", "uint32_t x = key % P;",
+                                     "test_shared_reservoirs_receive_arrivals_point_by_point_then_table_by_table"),
+    "shared_query_ignores_table": ("uint32_t x = pool_index(&s, t, key, P), m", "uint32_t x = pool_index(&s, 0, key, P), m",
+                                   "test_collision_free_pool_changes_nothing"),
 }
 
 

@@ -543,3 +543,92 @@ def test_adding_in_batches_continues_every_bucket_stream():
         oracle.add_rows(t, n, rp2, c.col[c.row_ptr[cut]:], cut, K, L, R, rb, seed)
         assert np.array_equal(t, et) and np.array_equal(n, ec), cut
     assert ec.max() > 4 * R
+
+
+# ----------------------------------------- reservoir sharing (Section 3.5)
+
+def test_shared_pool_map_is_uniform_and_independent_across_tables():
+    """Each bucket points to a uniformly random reservoir of the pool (chi-square over the pool), and
+    the reservoirs two tables pick for the same address are independent (chi-square over pairs)."""
+    from scipy import stats
+    P = 37
+    cells = np.zeros(P, dtype=np.int64)
+    pairs = np.zeros((P, P), dtype=np.int64)
+    for b in range(4000):
+        x0 = oracle.pool_index(0, b, P, 77)
+        x1 = oracle.pool_index(5, b, P, 77)
+        cells[x0] += 1
+        cells[x1] += 1
+        pairs[x0, x1] += 1
+    assert cells.min() >= 0 and int(cells.sum()) == 8000
+    assert stats.chisquare(cells).pvalue > 1e-4
+    small = np.zeros((6, 6), dtype=np.int64)  # pairs folded into 6 x 6 cells of ~equal mass
+    for i in range(P):
+        for j in range(P):
+            small[i * 6 // P, j * 6 // P] += pairs[i, j]
+    exp = np.outer(np.bincount(np.arange(P) * 6 // P, minlength=6), np.bincount(np.arange(P) * 6 // P,
+                                                                               minlength=6)) * 4000 / P / P
+    assert stats.chisquare(small.ravel(), f_exp=exp.ravel() * small.sum() / exp.sum()).pvalue > 1e-4
+
+
+def test_shared_reservoirs_receive_arrivals_point_by_point_then_table_by_table():
+    """R above every shared reservoir's size: reservoir x holds exactly the (point, table) arrivals
+    whose bucket points to x, in Algorithm 2's loop order (points in id order, tables in order),
+    found here by enumerating the keys; every arrival lands in one reservoir."""
+    c = _small_workload(n=900, seed=13)
+    K, L, rb, seed, P = 2, 5, 8, 31, 600
+    ks = oracle.keys(c.row_ptr, c.col, K, L, rb, seed)
+    nonempty = np.diff(c.row_ptr) > 0
+    streams = collections.defaultdict(list)
+    for p in range(c.n_rows):
+        if not nonempty[p]:
+            continue
+        for t in range(L):
+            streams[oracle.pool_index(t, int(ks[t, p]), P, seed)].append(p)
+    R = max(len(v) for v in streams.values())
+    tables, counts = oracle.build_tables_shared(c.row_ptr, c.col, K, L, R, rb, seed, P)
+    assert int(counts.sum()) == L * int(nonempty.sum())
+    for x in range(P):
+        got = tables[x]
+        exp = streams.get(x, [])
+        assert counts[x] == len(exp)
+        assert got[:len(exp)].tolist() == exp and np.all(got[len(exp):] == -1)
+
+
+def test_one_shared_reservoir_closed_form():
+    """P = 1 with R above L * (non-empty rows): the one reservoir holds every point L times in a
+    row, and every query gathers it L times, so every other non-empty point counts L^2; the top-k
+    is the smallest such ids."""
+    c = _small_workload(n=60, seed=5)
+    K, L, rb, seed, k = 2, 3, 6, 9, 12
+    nonempty = np.nonzero(np.diff(c.row_ptr) > 0)[0]
+    R = L * len(nonempty)
+    tables, counts = oracle.build_tables_shared(c.row_ptr, c.col, K, L, R, rb, seed, 1)
+    assert tables[0].tolist() == np.repeat(nonempty, L).tolist() and counts[0] == R
+    q = np.array([int(nonempty[3]), int(nonempty[0])])
+    sub = c.rows(q)
+    ids, cnt = oracle.query_shared(tables, counts, K, L, R, rb, seed, 1, sub.row_ptr, sub.col, k,
+                                   exclude=q.astype(np.int32))
+    for i, qq in enumerate(q):
+        exp = [int(x) for x in nonempty if x != qq][:k]
+        assert ids[i].tolist() == exp + [-1] * (k - len(exp))
+        assert cnt[i].tolist() == [L * L] * len(exp) + [0] * (k - len(exp))
+
+
+def test_collision_free_pool_changes_nothing():
+    """A pool so large that no two used buckets share a reservoir, with R above every occupancy:
+    every query gathers exactly the unshared index's buckets, so the graphs agree."""
+    c = _small_workload(n=700, seed=21)
+    K, L, rb, k = 2, 6, 7, 15
+    P = 2**20
+    for seed in range(50, 80):  # a seed whose used buckets map to distinct reservoirs
+        ks = oracle.keys(c.row_ptr, c.col, K, L, rb, seed)
+        used = {(t, int(b)) for t in range(L) for b in np.unique(ks[t])}
+        if len({oracle.pool_index(t, b, P, seed) for t, b in used}) == len(used):
+            break
+    else:
+        pytest.fail("no collision-free seed")
+    R = _max_occupancy(ks)
+    ei, en = oracle.knn_graph(c.row_ptr, c.col, K, L, R, rb, seed, k)
+    si, sn = oracle.knn_graph_shared(c.row_ptr, c.col, K, L, R, rb, seed, k, P)
+    assert np.array_equal(ei, si) and np.array_equal(en, sn)
