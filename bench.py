@@ -424,6 +424,8 @@ def kdd12_section(fl, args) -> dict:
 
     ms = _timed(step, 3)
     ph = _phases(fl, step, 2)
+    qual_q = torch.from_numpy(synth.sample_rows(n, 1000, seed=41).astype(np.int32)).cuda()
+    qual = fl.quality(dev, qual_q, ids[qual_q.long()].contiguous())
     plain_ms = _timed(lambda: fl.flash_knn_graph_plain(params, dev, k, ids, cnt, stream), 1)
     plain_ph = _phases(fl, lambda: fl.flash_knn_graph_plain(params, dev, k, ids, cnt, stream), 1)
     torch.cuda.synchronize()
@@ -434,8 +436,27 @@ def kdd12_section(fl, args) -> dict:
     keys_ms = _timed(lambda: fl.flash_keys(params, dev, keys, stream), 3)
     ix = fl.flash_build(params, dev)
     m_total = _candidates(fl, ix, keys, p.R)
+    index_bytes = ix.info()["bytes"]
     ix.free()
-    del keys, ids, cnt, dev
+    del keys
+    torch.cuda.empty_cache()
+    # reservoir sharing (Section 3.5): one pool of F * L * 2^rb reservoirs for all tables
+    T = 1 << p.range_bits
+    share = {}
+    for F in (0.3,):
+        P = int(round(F * p.L * T))
+        ps = fl.FlashParams(p.K, p.L, p.R, p.range_bits, p.seed, share_pool=P)
+        s_ms = _timed(lambda: fl.flash_knn_graph(ps, dev, k, ids, cnt, stream), 2)
+        s_qual = fl.quality(dev, qual_q, ids[qual_q.long()].contiguous())
+        ixs = fl.flash_build(ps, dev)
+        s_bytes = ixs.info()["bytes"]
+        ixs.free()
+        share[str(F)] = {"pool_reservoirs": P, "graph_ms": s_ms, "queries_per_s": n / (s_ms / 1e3),
+                         "R@k": s_qual["R@k"], "S@k": s_qual["S@k"], "index_bytes": s_bytes,
+                         "dense_table_bytes": 4 * P * (p.R + 1)}
+    share["1.0 (no sharing)"] = {"graph_ms": ms, "R@k": qual["R@k"], "S@k": qual["S@k"], "index_bytes": index_bytes,
+                                 "dense_table_bytes": 4 * p.L * T * (p.R + 1)}
+    del ids, cnt, dev
     torch.cuda.empty_cache()
     peak, src = _peak()
     T = 1 << p.range_bits
@@ -452,6 +473,9 @@ def kdd12_section(fl, args) -> dict:
             "phases_ms": ph, "plain_graph_ms": plain_ms, "plain_queries_per_s": n / (plain_ms / 1e3),
             "plain_phases_ms": plain_ph, "speedup_vs_plain": plain_ms / ms,
             "candidates_per_query": m_total / n, "peak_GB/s": peak, "peak_source": src,
+            "quality": {"queries": int(qual_q.numel()), "k": k, "R@k": qual["R@k"], "S@k": qual["S@k"],
+                        "gold_standard": "cosine of column sets over all rows (flash_eval_quality)"},
+            "reservoir_sharing": share,
             "rooflines": {
                 "hash_phase (keys, 8(N+1)+4nnz+4LN)": roof(b_keys, ph.get("hash", keys_ms)),
                 "sort+reservoir (4LN keys read + 4LN ids + 4L(T+1) starts written)":
@@ -632,6 +656,14 @@ def main():
             "bytes_formula": "8(N+1) + 4 nnz + 4 K L N", "keys_epilogue_GB/s": keys_bytes / (keys_ms / 1e3) / 1e9,
             "keys_frac_of_hbm_peak": keys_bytes / (keys_ms / 1e3) / 1e9 / peak}
 
+    # Section 4.3's quality measures of the graph on 1000 sampled rows (brute force on the GPU)
+    from paper_1709_01190_gb300 import synth as _sy
+    qq = torch.from_numpy(_sy.sample_rows(n, min(1000, n), seed=41).astype(np.int32)).cuda()
+    step()
+    qres = fl.quality(dev, qq, ids[qq.long()].contiguous())
+    quality = {"queries": int(qq.numel()), "k": k, "R@k": qres["R@k"], "S@k": qres["S@k"],
+               "gold_standard": "cosine of column sets over all rows (flash_eval_quality)"}
+
     # the plain, unbatched GPU path on the same rows (same results; a baseline)
     plain = None
     if world == 1:
@@ -702,7 +734,7 @@ def main():
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded, webspam-shaped; see config)",
                 "config": config_of(w, csr), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-                "phases_ms": acc, "doph": doph, "plain": plain, "densify": densify,
+                "phases_ms": acc, "doph": doph, "plain": plain, "densify": densify, "quality": quality,
                 "graph_replay_ms_per_step": graph_ms, "tuning": tuned,
                 "config3_url_like_batch": config3, "config4_kdd12_like_graph": config4,
                 "served": served, "reduced": bool(args.rows)}

@@ -59,7 +59,8 @@ enum {
  * Section 3.2: reservoirs of size R; Section 4.4.1: 2^range_bits buckets
  * per table).  Limits of the library: K, L, R >= 1; K*L <= 4096;
  * 1 <= range_bits <= 30; L*R <= 16384 (count table of one query); L <= 256
- * and n_rows < 2^24 - 1 for the packed (id, count) query table. */
+ * and n_rows < 2^24 - 1 for the packed (id, count) query table; with
+ * reservoir sharing L * n_rows <= 2^32 - 2^24. */
 typedef struct flash_params {
   uint32_t K;
   uint32_t L;
@@ -74,7 +75,15 @@ typedef struct flash_params {
    * bin to the right).  Other values are FLASH_EINVAL.  Zero-initialised
    * callers get rotation. */
   uint32_t densify;
-  uint32_t reserved; /* must be 0 */
+  /* Reservoir sharing (Section 3.5): 0 = every bucket has its own reservoir;
+   * P > 0 (at most 2^30) = one pool of P reservoirs serves all L tables (the
+   * paper's F = P / (L * 2^range_bits)); bucket b of table t points to pool
+   * reservoir ((SplitMix64 mix of (t, b) keyed by the seed) * P) >> 32, a
+   * shared reservoir receives its arrivals point by point and, for each
+   * point, table by table, and a query gathers the reservoir of each of its L
+   * buckets.  flash_add and flash_knn_graph_plain do not support it
+   * (FLASH_EINVAL); flash_index_export then writes [P][R] and [P]. */
+  uint32_t share_pool;
 } flash_params;
 
 /* A sparse matrix in CSR form; all pointers are DEVICE pointers.
@@ -196,6 +205,23 @@ int flash_knn_graph_plain(const flash_params *p, const flash_csr *x, int32_t k, 
 int flash_knn_graph_host(const flash_params *p, const int64_t *row_ptr, const int32_t *col, int64_t n_rows,
                          int64_t dim, int32_t k, int32_t *out_ids, int32_t *out_counts, void *stream);
 
+/* Quality measures of Section 4.3 by brute force: for every query row, its
+ * nearest neighbour under the cosine of column sets (the gold standard; rows
+ * hold distinct column ids; ties to the smaller id; rows without entries have
+ * cosine 0 with every row) and the mean cosine of its reported ids.
+ *   x                : the indexed rows (DEVICE CSR)
+ *   queries          : DEVICE int32 [nq], row ids of x
+ *   reported         : DEVICE int32 [nq][k], the ids a query reported (-1 = none)
+ *   nn               : DEVICE int32 [nq], the nearest other row
+ *   nn_sim, sim_at_k : DEVICE float64 [nq], its cosine, and the mean cosine of
+ *                      the reported ids (-1 left out; 0 when none)
+ * R@k is then the share of queries whose nn is among their reported ids, S@k
+ * the mean of sim_at_k.  Scratch: 4 * dim bytes and a little more.  The call
+ * synchronizes `stream`; FLASH_EDATA if some query has more than 512 rows tied
+ * (within rounding) for its nearest neighbour. */
+int flash_eval_quality(const flash_csr *x, const int32_t *queries, int64_t nq, const int32_t *reported, int32_t k,
+                       int32_t *nn, double *nn_sim, double *sim_at_k, void *stream);
+
 /* Release an index (frees its device memory after the work queued on the
  * stream it was built on).  NULL is ignored. */
 void flash_index_free(flash_index *index);
@@ -205,7 +231,9 @@ int flash_index_get_info(const flash_index *index, flash_index_info *info);
 /* Dense copy of the tables, for inspection and tests:
  *   tables : DEVICE int32 [L][2^range_bits][R]; slot s of bucket b of table t;
  *            -1 where the reservoir holds fewer than s+1 ids
- *   counts : DEVICE uint32 [L][2^range_bits]; arrivals per bucket (not capped) */
+ *   counts : DEVICE uint32 [L][2^range_bits]; arrivals per bucket (not capped)
+ * With reservoir sharing (share_pool = P): tables [P][R], counts [P], the
+ * reservoirs of the pool. */
 int flash_index_export(const flash_index *index, int32_t *tables, uint32_t *counts, void *stream);
 
 /* Synchronize `stream`, return the device error flag bits raised since the

@@ -47,6 +47,29 @@ def nearest_neighbours(sim, queries) -> np.ndarray:
     return np.argmax(s, axis=1)
 
 
+def nearest_neighbours_of_sets(row_ptr, col, dim, queries) -> np.ndarray:
+    """nearest_neighbours for the cosine of column sets, with ties decided exactly: the cosine
+    c / sqrt(|A| |B|) of two sets sharing c columns orders like c^2 / |B| for a fixed query, so
+    rows are compared by integer cross multiplication (Python integers) -- two rows whose cosines
+    are equal as numbers are a tie, which goes to the smaller id, whatever float rounding says."""
+    m = _matrix(row_ptr, col, None, dim)
+    lens = np.asarray(m.getnnz(axis=1), dtype=np.int64)
+    q = m[np.asarray(queries, dtype=np.int64)]
+    inter = (q @ m.T).tocsr()
+    out = np.empty(len(queries), dtype=np.int64)
+    for i, qq in enumerate(np.asarray(queries, dtype=np.int64)):
+        row = inter.getrow(i)
+        best = None  # (c, len, id)
+        for r, c in zip(row.indices.tolist(), np.rint(row.data).astype(np.int64).tolist()):
+            if r == qq or c <= 0:
+                continue
+            if best is None or c * c * best[1] > best[0] * best[0] * lens[r] or (
+                    c * c * best[1] == best[0] * best[0] * lens[r] and r < best[2]):
+                best = (c, int(lens[r]), r)
+        out[i] = best[2] if best is not None else (1 if qq == 0 else 0)
+    return out
+
+
 def recall_at_k(ids, nn) -> float:
     """R@k: the share of queries whose nearest neighbour is among their reported ids [nq][k]."""
     ids = np.asarray(ids)

@@ -22,7 +22,7 @@ from .build import build as _build_lib
 __all__ = [
     "FlashError", "FlashParams", "DeviceCSR", "FlashIndex", "build",
     "flash_hash", "flash_keys", "flash_build", "flash_add", "flash_query", "flash_knn_graph", "flash_knn_graph_plain",
-    "flash_knn_graph_host",
+    "flash_knn_graph_host", "flash_eval_quality", "quality",
     "flash_index_export", "flash_device_error", "flash_set_scratch_budget", "flash_knn_graph_scratch_bytes",
     "flash_query_scratch_bytes", "flash_strerror", "flash_version",
     "hash_rows", "row_keys", "knn_graph", "DEVERR_COL_RANGE", "DEVERR_ROW_PTR", "DEVERR_TIMEOUT",
@@ -37,17 +37,21 @@ def build(force: bool = False) -> str:
 @dataclasses.dataclass(frozen=True)
 class FlashParams:
     """K hashes per table, L tables (Section 2.2), reservoirs of R ids (Section 3.2),
-    2^range_bits buckets per table (Section 4.4.1), the seed of every random choice, and the
-    densification of empty bins (Section 2.3): 0 rotation, 1 optimal densification ([36])."""
+    2^range_bits buckets per table (Section 4.4.1), the seed of every random choice, the
+    densification of empty bins (Section 2.3): 0 rotation, 1 optimal densification ([36]), and
+    reservoir sharing (Section 3.5): 0 none, else one pool of share_pool reservoirs for all tables
+    (F = share_pool / (L * 2^range_bits))."""
     K: int
     L: int
     R: int
     range_bits: int
     seed: int
     densify: int = 0
+    share_pool: int = 0
 
     def c(self) -> Params:
-        return Params(self.K, self.L, self.R, self.range_bits, self.seed & ((1 << 64) - 1), self.densify, 0)
+        return Params(self.K, self.L, self.R, self.range_bits, self.seed & ((1 << 64) - 1), self.densify,
+                      self.share_pool)
 
     @property
     def B(self) -> int:
@@ -156,12 +160,13 @@ class FlashIndex:
             pass
 
     def export(self, stream=None):
-        """Dense (tables int32 [L][2^rb][R] with -1 = empty, counts uint32-as-int32 [L][2^rb])."""
+        """Dense (tables int32 [L][2^rb][R] with -1 = empty, counts uint32-as-int32 [L][2^rb]);
+        with reservoir sharing the pool's (tables [P][R], counts [P])."""
         import torch
         p = self.params
-        T = 1 << p.range_bits
-        tables = torch.empty((p.L, T, p.R), dtype=torch.int32, device="cuda")
-        counts = torch.empty((p.L, T), dtype=torch.int32, device="cuda")
+        shape = (p.share_pool,) if p.share_pool else (p.L, 1 << p.range_bits)
+        tables = torch.empty(shape + (p.R,), dtype=torch.int32, device="cuda")
+        counts = torch.empty(shape, dtype=torch.int32, device="cuda")
         flash_index_export(self, tables, counts, stream)
         return tables, counts
 
@@ -203,6 +208,28 @@ def flash_knn_graph_plain(params: FlashParams, x: DeviceCSR, k: int, out_ids, ou
     p, c = params.c(), x.c()
     check(lib().flash_knn_graph_plain(ctypes.byref(p), ctypes.byref(c), int(k), _ptr(out_ids), _ptr(out_counts),
                                       _stream(stream)), "flash_knn_graph_plain")
+
+
+def flash_eval_quality(x: DeviceCSR, queries, reported, nn, nn_sim, sim_at_k, stream=None) -> None:
+    """Section 4.3's gold standard by brute force on the GPU (see include/flash.h)."""
+    nq, k = int(reported.shape[0]), int(reported.shape[1])
+    c = x.c()
+    check(lib().flash_eval_quality(ctypes.byref(c), _ptr(queries), nq, _ptr(reported), k, _ptr(nn), _ptr(nn_sim),
+                                   _ptr(sim_at_k), _stream(stream)), "flash_eval_quality")
+
+
+def quality(x: DeviceCSR, queries, reported, stream=None) -> dict:
+    """R@k and S@k (Section 4.3) of the reported ids [nq][k] of the query rows `queries` (row ids
+    of x), with the per-query nearest neighbours."""
+    import torch
+    nq = int(queries.numel())
+    nn = torch.empty(nq, dtype=torch.int32, device="cuda")
+    nn_sim = torch.empty(nq, dtype=torch.float64, device="cuda")
+    sim = torch.empty(nq, dtype=torch.float64, device="cuda")
+    flash_eval_quality(x, queries, reported, nn, nn_sim, sim, stream)
+    hit = (reported == nn[:, None]).any(dim=1)
+    return {"R@k": float(hit.double().mean()), "S@k": float(sim.mean()), "nn": nn, "nn_sim": nn_sim,
+            "sim_at_k": sim}
 
 
 def flash_knn_graph_host(params: FlashParams, row_ptr, col, dim: int, k: int, out_ids, out_counts,

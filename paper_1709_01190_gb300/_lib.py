@@ -25,7 +25,7 @@ class FlashError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_uint32), ("L", ctypes.c_uint32), ("R", ctypes.c_uint32),
                 ("range_bits", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("densify", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("share_pool", ctypes.c_uint32)]
 
 
 class Csr(ctypes.Structure):
@@ -59,6 +59,7 @@ def lib():
             "flash_knn_graph": ([P, C, I32, VP, VP, VP], ctypes.c_int),
             "flash_query_noalloc": ([VP, C, I32, VP, VP, VP, VP], ctypes.c_int),
             "flash_knn_graph_plain": ([P, C, I32, VP, VP, VP], ctypes.c_int),
+            "flash_eval_quality": ([C, VP, I64, VP, I32, VP, VP, VP, VP], ctypes.c_int),
             "flash_knn_graph_host": ([P, VP, VP, I64, I64, I32, VP, VP, VP], ctypes.c_int),
             "flash_index_free": ([VP], None),
             "flash_index_get_info": ([VP, ctypes.POINTER(IndexInfo)], ctypes.c_int),

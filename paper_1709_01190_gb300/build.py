@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libflash.so")
-SOURCES = ["doph.cu", "sort.cu", "reservoir.cu", "query.cu", "flash_api.cu", "query_noalloc.cu", "plain.cu", "add.cu"]
+SOURCES = ["doph.cu", "sort.cu", "reservoir.cu", "query.cu", "flash_api.cu", "query_noalloc.cu", "plain.cu", "add.cu", "eval.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

@@ -17,6 +17,7 @@ namespace flash {
 //   r     : key of the reservoir decisions                     (Algorithm 1)
 struct Seeds {
   uint64_t a1, b1, a2, b2, r, d;  // d: key of the optimal-densification probes
+  uint64_t e;                     // key of the bucket -> reservoir map of reservoir sharing
 };
 
 __host__ __device__ inline uint64_t sm64_finalize(uint64_t z) {
@@ -27,8 +28,8 @@ __host__ __device__ inline uint64_t sm64_finalize(uint64_t z) {
 
 inline Seeds derive_seeds(uint64_t seed) {
   Seeds s;
-  uint64_t w[6];
-  for (int i = 0; i < 6; ++i) {
+  uint64_t w[7];
+  for (int i = 0; i < 7; ++i) {
     seed += 0x9E3779B97F4A7C15ULL;
     w[i] = sm64_finalize(seed);
   }
@@ -38,7 +39,25 @@ inline Seeds derive_seeds(uint64_t seed) {
   s.b2 = w[3];
   s.r = w[4];
   s.d = w[5];
+  s.e = w[6];
   return s;
+}
+
+// Reservoir sharing (Section 3.5): the reservoir of the shared pool of P that
+// bucket b of table t points to, ((F(e ^ (t * 2^32 + b)) >> 32) * P) >> 32
+// with F SplitMix64's output function.
+__host__ __device__ inline uint32_t pool_index(uint64_t e, uint32_t t, uint32_t b, uint32_t P) {
+  const uint64_t u = sm64_finalize(e ^ ((static_cast<uint64_t>(t) << 32) + b));
+  return static_cast<uint32_t>(((u >> 32) * P) >> 32);
+}
+// "Table" of the reservoir draws of a shared pool (no real table uses it).
+constexpr uint32_t kPoolTable = 0xFFFFFFFFu;
+
+// log2 of the smallest power of two >= P (at least 1).
+inline uint32_t pool_bits_of(uint32_t P) {
+  uint32_t b = 1;
+  while (b < 31 && (1u << b) < P) ++b;
+  return b;
 }
 
 // Constant added per step of rotation densification (2^32 / golden ratio).

@@ -46,6 +46,7 @@ struct DophParams {
   uint32_t dim_u32;  // dim clipped to 2^32-1 (columns are int32)
   uint32_t B, K, L, rb, W, G;  // W = bitmap words, G = summary words
   uint32_t densify;            // 0 rotation, 1 optimal densification
+  uint32_t pool, pool_bits;    // keys mode, reservoir sharing: reservoir of each key; sentinel 2^pool_bits
   uint32_t rows_per_grab;
   uint32_t bin_words;  // W * 33 rounded up to a multiple of 4 (room for either layout)
   uint32_t smem_words_per_warp;
@@ -161,7 +162,7 @@ __device__ __forceinline__ int next_word_circular(const uint32_t (&sw)[4], uint3
 template <bool KEYS>
 __device__ __forceinline__ void emit_empty(const DophParams &a, int64_t r, uint32_t lane) {
   if (KEYS) {
-    const uint32_t T = static_cast<uint32_t>(1ULL << a.rb);
+    const uint32_t T = static_cast<uint32_t>(1ULL << (a.pool ? a.pool_bits : a.rb));
     for (uint32_t t = lane; t < a.L; t += 32) {
       if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = T;
       if (a.out_rm) a.out_rm[r * a.L + t] = T;
@@ -222,7 +223,8 @@ __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const u
     for (uint32_t t = lane; t < a.L; t += 32) {
       uint64_t x = 0;
       for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[bix<PAD>(t + i * a.L)];
-      const uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
+      uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
+      if (a.pool) key = pool_index(a.s.e, t, key, a.pool);  // the shared reservoir the bucket points to
       if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
       if (a.out_rm) a.out_rm[r * a.L + t] = key;
     }
@@ -596,6 +598,8 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.smem_words_per_warp = a.bin_words + ((a.W + 3) & ~3u);
   a.s = L.seeds;
   a.densify = L.densify;
+  a.pool = L.keys ? L.pool : 0u;
+  a.pool_bits = L.pool_bits;
   a.out = L.out;
   a.out_rm = L.out_rowmajor;
   a.ld = L.ld;

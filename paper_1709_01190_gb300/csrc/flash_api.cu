@@ -147,7 +147,7 @@ class Arena {
 
 int check_hash_params(const flash_params *p) {
   if (!p || p->K < 1 || p->L < 1) return FLASH_EINVAL;
-  if (p->densify > 1 || p->reserved != 0) return FLASH_EINVAL;
+  if (p->densify > 1 || p->share_pool > (1u << 30)) return FLASH_EINVAL;
   if (static_cast<uint64_t>(p->K) * p->L > kMaxBins) return FLASH_EINVAL;
   return 0;
 }
@@ -182,6 +182,8 @@ DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, 
   d.L = p->L;
   d.range_bits = p->range_bits;
   d.densify = p->densify;
+  d.pool = p->share_pool;
+  d.pool_bits = p->share_pool ? pool_bits_of(p->share_pool) : 0u;
   d.seeds = s;
   d.keys = keys;
   d.out = out;
@@ -251,6 +253,97 @@ void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, in
   ar.add(&b.counters, 8);
 }
 
+// Reservoir sharing (p->share_pool = P > 0): one pool of P reservoirs for all
+// tables.  The L * n arrivals are sorted as ONE sequence in row-major (point,
+// table) order -- Algorithm 2's loop order -- by the reservoir their bucket
+// points to (the keys DOPH writes are already pool indices), so a stable sort
+// keeps every shared reservoir's arrivals in that order; the sorted entries
+// are positions p * L + t, turned into point ids after the reservoir step.
+struct SharedScratch {
+  uint32_t *keys_rm = nullptr, *tkeys = nullptr, *skeys = nullptr, *hist = nullptr, *seg = nullptr;
+  int32_t *tids = nullptr, *tids2 = nullptr;
+  uint64_t *heavy = nullptr;
+  unsigned long long *counters = nullptr;
+  int64_t heavy_cap = 0;
+  uint32_t pool_bits = 0;
+  SortPlan plan{};
+  RowOrder ro;
+  flash_tuning tu{};
+};
+
+void plan_build_shared(Arena &ar, SharedScratch &b, const flash_params *p, int64_t n) {
+  const int64_t ln = static_cast<int64_t>(p->L) * n;
+  b.tu = current_tuning();
+  b.ro.plan(ar, b.tu, n);
+  b.pool_bits = pool_bits_of(p->share_pool);
+  b.plan = make_sort_plan(b.pool_bits, ln, 1);
+  b.heavy_cap = reservoir_heavy_capacity(ln, 1, p->R, b.pool_bits);
+  ar.add(&b.keys_rm, ln);
+  ar.add(&b.tkeys, ln);
+  ar.add(&b.tids, ln);
+  if (b.plan.passes > 1) {
+    ar.add(&b.skeys, ln);
+    ar.add(&b.tids2, ln);
+    ar.add(&b.seg, b.plan.seg_words);
+  }
+  ar.add(&b.hist, b.plan.hist_words);
+  ar.add(&b.heavy, b.heavy_cap);
+  ar.add(&b.counters, 8);
+}
+
+// ids [L * n] and starts [2^pool_bits + 1] of a shared pool
+int run_build_shared(const flash_params *p, const Seeds &s, const flash_csr *x, SharedScratch &b, int32_t *ids,
+                     uint32_t *starts, cudaStream_t st) {
+  const int64_t n = x->n_rows, ln = static_cast<int64_t>(p->L) * n;
+  g_timer.mark("hash", st);
+  DophLaunch dl = doph_args(p, s, x, true, nullptr, n, b.counters, b.tu);
+  dl.out_rowmajor = b.keys_rm;
+  int rc = b.ro.apply(dl, x, st);
+  if (!rc) rc = launch_doph(dl, st);
+  if (rc) return rc;
+  g_timer.mark("sort", st);
+  SortLaunch sl{};
+  sl.keys_in = b.keys_rm;
+  sl.n = ln;
+  sl.L = 1;
+  sl.range_bits = b.pool_bits;
+  sl.ids_out = ids;
+  sl.tmp_keys = b.tkeys;
+  sl.tmp_ids = b.tids;
+  sl.keys_out = b.skeys;
+  sl.tmp_ids2 = b.tids2;
+  sl.hist = b.hist;
+  sl.seg = b.seg;
+  sl.starts = starts;
+  sl.claim = b.counters + 2;
+  sl.R = p->R;
+  sl.heavy_count = b.counters + 1;
+  sl.heavy = b.heavy;
+  sl.heavy_cap = b.heavy_cap;
+  if ((rc = sort_tables(b.plan, sl, st))) return rc;
+  g_timer.mark("reservoir", st);
+  ReservoirLaunch rl{};
+  rl.ids = ids;
+  rl.starts = starts;
+  rl.n = ln;
+  rl.L = 1;
+  rl.R = p->R;
+  rl.range_bits = b.pool_bits;
+  rl.r = s.r;
+  rl.shared = true;
+  rl.heavy_count = b.counters + 1;
+  rl.heavy = b.heavy;
+  rl.heavy_cap = b.heavy_cap;
+  rl.heavy_listed = true;
+  if ((rc = launch_reservoir(rl, st))) return rc;
+  return launch_positions_to_ids(ids, ln, p->L, st);
+}
+
+int64_t index_starts_words(const flash_params *p) {
+  return p->share_pool ? (1LL << pool_bits_of(p->share_pool)) + 1
+                       : static_cast<int64_t>(p->L) * ((1LL << p->range_bits) + 1);
+}
+
 // K1 (keys) -> K2 -> K3 into (ids, starts); without K3 when reservoir is false
 // (a batch that continues an index: its draws follow the stored counts)
 int run_build(const flash_params *p, const Seeds &s, const flash_csr *x, BuildScratch &b, int32_t *ids,
@@ -314,7 +407,8 @@ QueryLaunch query_args(const flash_params *p, const uint32_t *qkeys, bool rowmaj
   q.n = n;
   q.L = p->L;
   q.R = p->R;
-  q.range_bits = p->range_bits;
+  q.range_bits = p->share_pool ? pool_bits_of(p->share_pool) : p->range_bits;
+  q.shared = p->share_pool != 0;
   q.k = k;
   q.exclude = exclude;
   q.exclude_self = exclude_self;
@@ -394,17 +488,19 @@ int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, vo
   if (int rc = check_params(p)) return rc;
   if (int rc = check_csr(x)) return rc;
   if (x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
+  if (p->share_pool && static_cast<uint64_t>(p->L) * static_cast<uint64_t>(x->n_rows) > (1ull << 32) - (1ull << 24))
+    return FLASH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = x->n_rows;
-  const int64_t T1 = (1LL << p->range_bits) + 1;
   flash_index *ix = new (std::nothrow) flash_index();
   if (!ix) return FLASH_ENOMEM;
   ix->p = *p;
   ix->s = derive_seeds(p->seed);
   ix->n = n;
   cudaGetDevice(&ix->device);
+  ix->pool_bits = p->share_pool ? pool_bits_of(p->share_pool) : 0u;
   const size_t ids_b = sizeof(int32_t) * static_cast<size_t>(p->L) * static_cast<size_t>(n > 0 ? n : 1);
-  const size_t st_b = sizeof(uint32_t) * static_cast<size_t>(p->L) * static_cast<size_t>(T1);
+  const size_t st_b = sizeof(uint32_t) * static_cast<size_t>(index_starts_words(p));
   if (cudaMalloc(&ix->ids, ids_b) != cudaSuccess || cudaMalloc(&ix->starts, st_b) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(ix->ids);
@@ -414,7 +510,15 @@ int flash_build(const flash_params *p, const flash_csr *x, flash_index **out, vo
   }
   ix->bytes = static_cast<int64_t>(ids_b + st_b);
   int rc = 0;
-  {
+  if (p->share_pool && n == 0) {
+    rc = cuda_ok(cudaMemsetAsync(ix->starts, 0, st_b, st));
+  } else if (p->share_pool) {
+    Arena ar;
+    SharedScratch b;
+    plan_build_shared(ar, b, p, n);
+    rc = ar.alloc(st);
+    if (!rc) rc = run_build_shared(p, ix->s, x, b, ix->ids, ix->starts, st);
+  } else {
     Arena ar;
     BuildScratch b;
     plan_build(ar, b, p, n, x->nnz);
@@ -440,6 +544,7 @@ int flash_add(flash_index *ix, const flash_csr *x, void *stream) {
   if (ix->n + x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const flash_params *p = &ix->p;
+  if (p->share_pool) return FLASH_EINVAL;
   const int64_t n_old = ix->n, n_new = x->n_rows, n = n_old + n_new;
   const int64_t T1 = (1LL << p->range_bits) + 1;
   int cur_dev = 0;
@@ -552,9 +657,31 @@ int flash_knn_graph(const flash_params *p, const flash_csr *x, int32_t k, int32_
   if (x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
   if (x->n_rows > 0 && (!out_ids || !out_counts)) return FLASH_EINVAL;
   if (x->n_rows == 0) return 0;
+  if (p->share_pool && static_cast<uint64_t>(p->L) * static_cast<uint64_t>(x->n_rows) > (1ull << 32) - (1ull << 24))
+    return FLASH_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = x->n_rows;
   const Seeds s = derive_seeds(p->seed);
+  if (p->share_pool) {
+    Arena ar;
+    SharedScratch b;
+    plan_build_shared(ar, b, p, n);
+    int32_t *ids = nullptr;
+    uint32_t *starts = nullptr;
+    int64_t *overflow = nullptr;
+    ar.add(&ids, static_cast<int64_t>(p->L) * n);
+    ar.add(&starts, index_starts_words(p));
+    ar.add(&overflow, n);
+    if (int rc = ar.alloc(st)) return rc;
+    g_timer.begin();
+    if (int rc = run_build_shared(p, s, x, b, ids, starts, st)) return rc;
+    g_timer.mark("query", st);
+    const int rc = launch_query(query_args(p, b.keys_rm, true, n, n, ids, starts, n, k, nullptr, true, out_ids,
+                                           out_counts, b.counters + 4, overflow),
+                                st);
+    g_timer.mark("end", st);
+    return rc;
+  }
   Arena ar;
   BuildScratch b;
   plan_build(ar, b, p, n, x->nnz, true);
@@ -581,7 +708,7 @@ int flash_knn_graph_plain(const flash_params *p, const flash_csr *x, int32_t k, 
                           int32_t *out_counts, void *stream) {
   if (int rc = check_params(p)) return rc;
   if (int rc = check_csr(x)) return rc;
-  if (k < 1 || k > 1024) return FLASH_EINVAL;
+  if (k < 1 || k > 1024 || p->share_pool) return FLASH_EINVAL;
   reset_launch_count();
   if (x->n_rows > kMaxPointsPacked) return FLASH_EINVAL;
   // the sort keys t * (2^rb + 1) + address must fit 32 bits
@@ -644,6 +771,44 @@ int flash_knn_graph_plain(const flash_params *p, const flash_csr *x, int32_t k, 
   const int rc = launch_plain_query(q, n, st);
   g_timer.mark("end", st);
   return rc;
+}
+
+int flash_eval_quality(const flash_csr *x, const int32_t *queries, int64_t nq, const int32_t *reported, int32_t k,
+                       int32_t *nn, double *nn_sim, double *sim_at_k, void *stream) {
+  reset_launch_count();
+  if (int rc = check_csr(x)) return rc;
+  if (nq < 0 || k < 1 || (nq > 0 && (!queries || !reported || !nn || !nn_sim || !sim_at_k))) return FLASH_EINVAL;
+  if (x->n_rows >= (1LL << 31) || x->dim > 0xFFFFFFFFLL) return FLASH_EINVAL;
+  if (nq == 0) return 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  EvalLaunch l{};
+  l.row_ptr = x->row_ptr;
+  l.col = x->col;
+  l.n = x->n_rows;
+  l.dim = x->dim;
+  l.queries = queries;
+  l.nq = nq;
+  l.reported = reported;
+  l.k = k;
+  l.nn = nn;
+  l.nn_sim = nn_sim;
+  l.sim_at_k = sim_at_k;
+  Arena ar;
+  ar.add(&l.mask, x->dim);
+  ar.add(&l.best, 32);
+  ar.add(&l.cand, 2LL * 32 * eval_candidate_capacity());
+  ar.add(&l.ncand, 32);
+  ar.add(&l.overflow, 1);
+  ar.add(&l.cos_slot, 32LL * k);
+  if (int rc = ar.alloc(st)) return rc;
+  if (int rc = launch_eval(l, st)) return rc;
+  uint32_t over = 0;
+  if (cudaMemcpyAsync(&over, l.overflow, sizeof(over), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return FLASH_ECUDA;
+  }
+  return over ? FLASH_EDATA : 0;
 }
 
 // Device address of host memory at p when the device can read it in place
@@ -720,8 +885,11 @@ int flash_index_get_info(const flash_index *ix, flash_index_info *info) {
 
 int flash_index_export(const flash_index *ix, int32_t *tables, uint32_t *counts, void *stream) {
   if (!ix || !tables || !counts) return FLASH_EINVAL;
-  return launch_export(ix->ids, ix->starts, ix->n, ix->p.L, ix->p.R, ix->p.range_bits, tables, counts,
-                       static_cast<cudaStream_t>(stream));
+  if (ix->p.share_pool)
+    return launch_export(ix->ids, ix->starts, static_cast<int64_t>(ix->p.L) * ix->n, 1, ix->p.R, ix->pool_bits,
+                         ix->p.share_pool, tables, counts, static_cast<cudaStream_t>(stream));
+  return launch_export(ix->ids, ix->starts, ix->n, ix->p.L, ix->p.R, ix->p.range_bits, 1u << ix->p.range_bits, tables,
+                       counts, static_cast<cudaStream_t>(stream));
 }
 
 uint32_t flash_device_error(void *stream) {
@@ -740,13 +908,18 @@ size_t flash_set_scratch_budget(size_t bytes) { return g_scratch_budget.exchange
 size_t flash_knn_graph_scratch_bytes(const flash_params *p, int64_t n_rows) {
   if (check_params(p) || n_rows < 0) return 0;
   Arena ar;
-  BuildScratch b;
-  plan_build(ar, b, p, n_rows, static_cast<int64_t>(p->L) * n_rows, true);  // same scratch either way
+  if (p->share_pool) {
+    SharedScratch b;
+    plan_build_shared(ar, b, p, n_rows);
+  } else {
+    BuildScratch b;
+    plan_build(ar, b, p, n_rows, static_cast<int64_t>(p->L) * n_rows, true);  // same scratch either way
+  }
   int32_t *ids = nullptr;
   uint32_t *starts = nullptr;
   int64_t *overflow = nullptr;
   ar.add(&ids, static_cast<int64_t>(p->L) * n_rows);
-  ar.add(&starts, static_cast<int64_t>(p->L) * ((1LL << p->range_bits) + 1));
+  ar.add(&starts, index_starts_words(p));
   ar.add(&overflow, n_rows);
   return ar.bytes();
 }

@@ -14,6 +14,9 @@ struct flash_index {
   int device;
   int32_t *ids;       // [L][n]: points grouped by bucket; reservoir = first min(m, R) of a segment
   uint32_t *starts;   // [L][2^rb + 1]
+  // reservoir sharing (p.share_pool = P > 0): one pool for every table, ids [L * n]
+  // grouped by reservoir, starts [2^pool_bits + 1] (reservoirs >= P empty)
+  uint32_t pool_bits;
   int64_t bytes;
 };
 
@@ -31,6 +34,7 @@ struct DophLaunch {
   int64_t n_rows, nnz, dim;
   uint32_t K, L, range_bits;
   uint32_t densify;  // 0 rotation, 1 optimal densification
+  uint32_t pool, pool_bits;  // keys mode, reservoir sharing: reservoir of each key (pool = P > 0); sentinel 2^pool_bits
   Seeds seeds;
   bool keys;         // false: out = hashes [n_rows][K*L]; true: out = keys [L][ld] (or null)
   uint32_t *out;
@@ -91,6 +95,7 @@ struct ReservoirLaunch {
   int64_t n;
   uint32_t L, R, range_bits;
   uint64_t r;                // reservoir key
+  bool shared;               // one pool of reservoirs (draws keyed by table 2^32 - 1)
   unsigned long long *heavy_count;  // 8 bytes of scratch
   uint64_t *heavy;           // list of (t << 32 | b), capacity heavy_cap
   int64_t heavy_cap;
@@ -112,6 +117,7 @@ struct QueryLaunch {
   const int32_t *exclude;    // [nq] or null
   bool exclude_self;         // exclude id q from query q (all-points graph)
   int32_t *out_ids, *out_counts;  // [nq][k]
+  bool shared;               // reservoir sharing: every table reads the one pool (ids, starts)
   unsigned long long *counters;   // 3 x 8 bytes of scratch
   int64_t *overflow;         // [nq] scratch
   uint32_t warp_table;       // 0 = automatic; else power of two
@@ -185,8 +191,31 @@ struct AddLaunch {
 };
 int launch_add(const AddLaunch &a, cudaStream_t stream);
 
-// ---- dense export of the tables
+// ---- quality measures of Section 4.3 by brute force (eval.cu)
+struct EvalLaunch {
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int64_t n, dim;
+  const int32_t *queries;   // [nq] row ids
+  int64_t nq;
+  const int32_t *reported;  // [nq][k]
+  int32_t k;
+  int32_t *nn;              // [nq] nearest neighbour
+  double *nn_sim, *sim_at_k;  // [nq]
+  uint32_t *mask;           // [dim] scratch
+  unsigned long long *best; // [32] scratch
+  uint32_t *cand;           // [32][capacity][2] scratch
+  uint32_t *ncand;          // [32] scratch
+  uint32_t *overflow;       // [1] scratch: a tie list overflowed
+  double *cos_slot;         // [32][k] scratch
+};
+uint32_t eval_candidate_capacity();
+int launch_eval(const EvalLaunch &l, cudaStream_t stream);
+
+// ---- dense export of the tables: [L][nb][R] and [L][nb] from starts [L][2^rb + 1]
 int launch_export(const int32_t *ids, const uint32_t *starts, int64_t n, uint32_t L, uint32_t R, uint32_t range_bits,
-                  int32_t *tables, uint32_t *counts, cudaStream_t stream);
+                  uint32_t nb, int32_t *tables, uint32_t *counts, cudaStream_t stream);
+// point ids from positions in the row-major (point, table) order of a shared pool: ids[i] /= L
+int launch_positions_to_ids(int32_t *ids, int64_t n, uint32_t L, cudaStream_t stream);
 
 }  // namespace flash

@@ -64,6 +64,7 @@ struct QArgs {
   const int32_t *ids;
   const uint32_t *starts;
   int64_t n;
+  int64_t st_stride, id_stride;  // table t's starts at t * st_stride, its ids at t * id_stride (0: one shared pool)
   uint32_t L, R, T;
   int32_t k;
   uint32_t kp;  // next power of two >= k
@@ -197,7 +198,7 @@ __device__ __forceinline__ void load_ranges(const G &g, const QArgs &a, const ui
     s[i] = 0;
     e[i] = 0;
     if (t < a.L && keys[i] < a.T) {
-      const uint32_t *st = a.starts + static_cast<int64_t>(t) * (static_cast<int64_t>(a.T) + 1);
+      const uint32_t *st = a.starts + static_cast<int64_t>(t) * a.st_stride;
       s[i] = ld_l2(st + keys[i], keep);
       e[i] = ld_l2(st + keys[i] + 1, keep);
     }
@@ -273,7 +274,7 @@ __device__ __forceinline__ void load_ids(const G &g, const QArgs &a, const uint3
     if (idx < M) {
       uint32_t t = cell[idx >> 2];
       while (pre[t + 1] <= idx) ++t;
-      idv[j] = ld_l2(a.ids + static_cast<int64_t>(t) * a.n + sb[t] + (idx - pre[t]), keep);
+      idv[j] = ld_l2(a.ids + static_cast<int64_t>(t) * a.id_stride + sb[t] + (idx - pre[t]), keep);
     }
   }
 }
@@ -384,7 +385,7 @@ __device__ uint32_t build_streams(const BlockGroup &g, const QArgs &a, const Reg
     uint32_t s = 0, e = 0;
     if (key < a.T) {
       const uint64_t keep = l2_policy_keep();
-      const uint32_t *st = a.starts + static_cast<int64_t>(t) * (static_cast<int64_t>(a.T) + 1);
+      const uint32_t *st = a.starts + static_cast<int64_t>(t) * a.st_stride;
       s = ld_l2(st + key, keep);
       e = ld_l2(st + key + 1, keep);
     }
@@ -408,7 +409,7 @@ __device__ uint32_t build_streams(const BlockGroup &g, const QArgs &a, const Reg
   long long *of = r.off + warp * kMaxTabPerWarp;
   if (static_cast<uint32_t>(lane) < ntab) {
     wp[lane] = inc - v;
-    of[lane] = static_cast<long long>(tt) * a.n + r.sbk[tt] - (inc - v);
+    of[lane] = static_cast<long long>(tt) * a.id_stride + r.sbk[tt] - (inc - v);
   }
   if (lane == 0) {
     wp[ntab] = total;
@@ -1153,6 +1154,8 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
   a.L = l.L;
   a.R = l.R;
   a.T = 1u << l.range_bits;
+  a.st_stride = l.shared ? 0 : static_cast<int64_t>(a.T) + 1;
+  a.id_stride = l.shared ? 0 : l.n;
   a.k = l.k;
   a.kp = next_pow2(static_cast<uint32_t>(l.k) < 2 ? 2 : static_cast<uint32_t>(l.k));
   a.exclude = l.exclude;

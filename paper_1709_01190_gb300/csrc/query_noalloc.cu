@@ -98,6 +98,8 @@ extern "C" int flash_query_noalloc(const flash_index *ix, const flash_csr *q, in
   d.L = p->L;
   d.range_bits = p->range_bits;
   d.densify = p->densify;
+  d.pool = p->share_pool;
+  d.pool_bits = ix->pool_bits;
   d.seeds = ix->s;
   d.keys = true;
   d.out = qkeys;
@@ -115,7 +117,8 @@ extern "C" int flash_query_noalloc(const flash_index *ix, const flash_csr *q, in
   l.n = ix->n;
   l.L = p->L;
   l.R = p->R;
-  l.range_bits = p->range_bits;
+  l.range_bits = p->share_pool ? ix->pool_bits : p->range_bits;
+  l.shared = p->share_pool != 0;
   l.k = k;
   l.exclude = exclude_ids;
   l.exclude_self = false;

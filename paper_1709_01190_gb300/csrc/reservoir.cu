@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) heavy_buckets_kernel(const uint32_t *star
 __global__ void __launch_bounds__(kResThreads) reservoir_select_kernel(int32_t *ids, const uint32_t *starts,
                                                                        int64_t n, uint32_t T, uint32_t R, uint64_t r,
                                                                        const unsigned long long *count,
-                                                                       const uint64_t *list, int64_t cap) {
+                                                                       const uint64_t *list, int64_t cap, bool shared) {
   extern __shared__ uint32_t win[];
   const int64_t nheavy = min(static_cast<int64_t>(*count), cap);
   for (int64_t h = blockIdx.x; h < nheavy; h += gridDim.x) {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kResThreads) reservoir_select_kernel(int32_t *
     int32_t *seg = ids + static_cast<int64_t>(t) * n + s;
     for (uint32_t j = threadIdx.x; j < R; j += blockDim.x) win[j] = j;
     __syncthreads();
-    const uint64_t bk = reservoir_bucket_key(r, t, b);
+    const uint64_t bk = reservoir_bucket_key(r, shared ? kPoolTable : t, b);
     for (uint32_t i = R + threadIdx.x; i < m; i += blockDim.x) {
       const uint32_t j = reservoir_draw(bk, i);
       if (j < R) atomicMax(&win[j], i);
@@ -67,13 +67,15 @@ __global__ void __launch_bounds__(kResThreads) reservoir_select_kernel(int32_t *
   }
 }
 
+// tables [L][nb][R], counts [L][nb] from starts [L][T + 1] (nb <= T buckets per table)
 __global__ void __launch_bounds__(256) export_kernel(const int32_t *ids, const uint32_t *starts, int64_t n, uint32_t T,
-                                                      uint32_t L, uint32_t R, int32_t *tables, uint32_t *counts) {
-  const int64_t total = static_cast<int64_t>(L) * T * R;
+                                                      uint32_t nb, uint32_t L, uint32_t R, int32_t *tables,
+                                                      uint32_t *counts) {
+  const int64_t total = static_cast<int64_t>(L) * nb * R;
   for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
        g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t tb = g / R, j = g - tb * R;
-    const int64_t t = tb / T, b = tb - t * T;
+    const int64_t t = tb / nb, b = tb - t * nb;
     const uint32_t *st = starts + t * (static_cast<int64_t>(T) + 1);
     const uint32_t s = st[b], m = st[b + 1] - s;
     tables[g] = j < m ? ids[t * n + s + j] : -1;
@@ -109,18 +111,34 @@ int launch_reservoir(const ReservoirLaunch &l, cudaStream_t stream) {
                            static_cast<int>(smem)) != cudaSuccess)
     return FLASH_ECUDA;
   reservoir_select_kernel<<<static_cast<unsigned>(num_sms() * 8), kResThreads, smem, stream>>>(
-      l.ids, l.starts, l.n, T, l.R, l.r, l.heavy_count, l.heavy, l.heavy_cap);
+      l.ids, l.starts, l.n, T, l.R, l.r, l.heavy_count, l.heavy, l.heavy_cap, l.shared);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }
 
 int launch_export(const int32_t *ids, const uint32_t *starts, int64_t n, uint32_t L, uint32_t R, uint32_t range_bits,
-                  int32_t *tables, uint32_t *counts, cudaStream_t stream) {
+                  uint32_t nb, int32_t *tables, uint32_t *counts, cudaStream_t stream) {
   const uint32_t T = 1u << range_bits;
-  const int64_t total = static_cast<int64_t>(L) * T * R;
+  const int64_t total = static_cast<int64_t>(L) * nb * R;
+  if (total == 0) return 0;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 65535LL * 16) blocks = 65535LL * 16;
-  export_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(ids, starts, n, T, L, R, tables, counts);
+  export_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(ids, starts, n, T, nb, L, R, tables, counts);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
+}
+
+// A shared pool is sorted as one sequence of the L * n (point, table) arrivals in
+// row-major order, so a sorted entry is an arrival's position p * L + t.
+__global__ void __launch_bounds__(256) positions_to_ids_kernel(int32_t *ids, int64_t n, uint32_t L) {
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    ids[i] = static_cast<int32_t>(static_cast<uint32_t>(ids[i]) / L);
+}
+
+int launch_positions_to_ids(int32_t *ids, int64_t n, uint32_t L, cudaStream_t stream) {
+  if (n == 0) return 0;
+  positions_to_ids_kernel<<<static_cast<unsigned>(8 * num_sms()), 256, 0, stream>>>(ids, n, L);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }

@@ -527,3 +527,89 @@ def test_add_rows_with_empty_rows_and_an_empty_batch():
     assert np.array_equal(u32(counts).reshape(ec.shape), ec)
     assert np.array_equal(tables.cpu().numpy(), et)
     ix.free()
+
+
+# ------------------------------------------------ reservoir sharing (Section 3.5)
+
+SHARE_CASES = [
+    ("tiny_plain", 5_000, dict(range_bits=9, R=8), 700, 0),          # F ~ 0.09: shared reservoirs overflow
+    ("tiny_plain", 3_000, dict(range_bits=6, R=4, L=6), 1, 0),        # one reservoir for every bucket
+    ("tiny_plain", 4_000, None, 150_000, 1),                         # optimal densification, F ~ 0.29
+    ("url_like_batched", 12_000, dict(range_bits=11), 80_000, 0),    # thousands of candidates per query
+    ("kdd12_like", 20_000, dict(range_bits=13, L=32), 70_000, 0),    # F ~ 0.27
+    ("kdd12_like", 8_000, dict(range_bits=12, L=16), 1_000_000, 0),  # a pool larger than the range (F ~ 15)
+]
+
+
+@pytest.mark.parametrize("name,n,over,P,densify", SHARE_CASES)
+def test_reservoir_sharing_tables_queries_and_graph(name, n, over, P, densify):
+    """Build, export, query and k-NN graph with one shared pool of P reservoirs, each against the
+    oracle's shared index, element by element."""
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p0 = _params_override(w, over)
+    p = fl.FlashParams(p0.K, p0.L, p0.R, p0.range_bits, p0.seed, densify=densify, share_pool=P)
+    dev = fl.DeviceCSR.from_host(c)
+    ix = fl.flash_build(p, dev)
+    tables, counts = ix.export()
+    et, ec = oracle.build_tables_shared(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, P, densify=densify)
+    assert np.array_equal(u32(counts), ec)
+    assert np.array_equal(tables.cpu().numpy(), et)
+    qids = synth.sample_rows(c.n_rows, min(300, c.n_rows), seed=17)
+    sub = c.rows(qids)
+    ids, cnt = fl.query(ix, fl.DeviceCSR.from_host(sub), w.k, torch.from_numpy(qids.astype(np.int32)).cuda())
+    ei, en = oracle.query_shared(et, ec, p.K, p.L, p.R, p.range_bits, p.seed, P, sub.row_ptr, sub.col, w.k,
+                                 exclude=qids.astype(np.int32), densify=densify)
+    assert np.array_equal(ids.cpu().numpy(), ei) and np.array_equal(cnt.cpu().numpy(), en)
+    gi, gc = fl.knn_graph(p, dev, w.k)
+    gei, gec = oracle.knn_graph_shared(c.row_ptr, c.col, p.K, p.L, p.R, p.range_bits, p.seed, w.k, P,
+                                       densify=densify)
+    assert np.array_equal(gi.cpu().numpy(), gei) and np.array_equal(gc.cpu().numpy(), gec)
+    assert fl.flash_device_error() == 0
+    ix.free()
+
+
+def test_reservoir_sharing_is_rejected_where_unsupported():
+    c = synth.generate(synth.WORKLOADS["tiny_plain"].data.replace(n_rows=500, n_clusters=10))
+    p = fl.FlashParams(2, 4, 4, 8, 3, share_pool=100)
+    dev = fl.DeviceCSR.from_host(c)
+    ix = fl.flash_build(p, dev)
+    with pytest.raises(fl.FlashError) as e:
+        fl.flash_add(ix, dev)
+    assert e.value.code == 1
+    with pytest.raises(fl.FlashError) as e:
+        fl.knn_graph_plain(p, dev, 5)
+    assert e.value.code == 1
+    with pytest.raises(fl.FlashError) as e:
+        fl.flash_build(fl.FlashParams(2, 4, 4, 8, 3, share_pool=(1 << 30) + 1), dev)
+    assert e.value.code == 1
+    ix.free()
+
+
+# ------------------------------------- quality measures of Section 4.3 (GPU evaluator)
+
+@pytest.mark.parametrize("name,n,over", [("tiny_plain", 6_000, None), ("kdd12_like", 40_000, dict(range_bits=14)),
+                                         ("url_like_batched", 15_000, dict(range_bits=12))])
+def test_quality_evaluator_matches_brute_force_cosines(name, n, over):
+    """flash_eval_quality: each query's nearest neighbour (exact, ties to the smaller id) equals the
+    oracle's, its cosine and the mean cosine of the reported ids agree to 1e-12, and R@k / S@k follow."""
+    from oracle import quality
+    w = synth.WORKLOADS[name].scaled(n)
+    c = synth.generate(w.data)
+    p = _params_override(w, over)
+    dev = fl.DeviceCSR.from_host(c)
+    ids, _ = fl.knn_graph(p, dev, w.k)
+    qs = synth.sample_rows(c.n_rows, 150, seed=31)
+    q_t = torch.from_numpy(qs.astype(np.int32)).cuda()
+    rep = ids[q_t.long()].contiguous()
+    got = fl.quality(dev, q_t, rep)
+    sim = quality.cosine_to_all(c.row_ptr, c.col, c.dim, qs)
+    nn = quality.nearest_neighbours_of_sets(c.row_ptr, c.col, c.dim, qs)
+    rep_np = rep.cpu().numpy()
+    assert np.array_equal(got["nn"].cpu().numpy(), nn)
+    assert np.allclose(got["nn_sim"].cpu().numpy(), sim[np.arange(len(qs)), nn], rtol=0, atol=1e-12)
+    per_q = np.array([sim[i, rep_np[i][rep_np[i] >= 0]].mean() if (rep_np[i] >= 0).any() else 0.0
+                      for i in range(len(qs))])
+    assert np.allclose(got["sim_at_k"].cpu().numpy(), per_q, rtol=0, atol=1e-12)
+    assert abs(got["R@k"] - quality.recall_at_k(rep_np, nn)) <= 1e-12
+    assert abs(got["S@k"] - quality.similarity_at_k(rep_np, sim)) <= 1e-12

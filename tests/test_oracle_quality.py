@@ -104,3 +104,45 @@ def test_flash_lists_find_planted_near_duplicates():
     s_flash = quality.similarity_at_k(ids[qs][planted], sim[planted])
     s_random = quality.similarity_at_k(rand[planted], sim[planted])
     assert s_flash > 1.5 * s_random, (s_flash, s_random)
+
+
+def test_exact_set_nearest_neighbours_agree_with_float_argmax_away_from_ties():
+    """The exact nearest neighbour of column sets equals the float64 argmax of the cosines except
+    where two cosines are equal as numbers (there the smaller id wins); on these rows, whose
+    planted near-duplicates make ties rare, the two agree wherever the best cosine is unique."""
+    from oracle import quality
+    from paper_1709_01190_gb300 import synth
+    c = synth.generate(synth.WORKLOADS["tiny_plain"].data.replace(n_rows=1500, n_clusters=80, seed=3))
+    qs = np.arange(0, c.n_rows, 7)
+    sim = quality.cosine_to_all(c.row_ptr, c.col, c.dim, qs)
+    nn_f = quality.nearest_neighbours(sim, qs)
+    nn_x = quality.nearest_neighbours_of_sets(c.row_ptr, c.col, c.dim, qs)
+    s2 = sim.copy()
+    s2[np.arange(len(qs)), qs] = -np.inf
+    best = s2.max(axis=1)
+    unique = (np.abs(s2 - best[:, None]) <= 1e-12 * np.maximum(best[:, None], 1e-300)).sum(axis=1) == 1
+    assert unique.mean() > 0.5
+    assert np.array_equal(nn_f[unique], nn_x[unique])
+    # where the best cosine is shared, the exact answer is the smallest id among the tied rows
+    for i in np.nonzero(~unique)[0]:
+        tied = np.nonzero(np.abs(s2[i] - best[i]) <= 1e-12 * max(best[i], 1e-300))[0]
+        assert nn_x[i] == tied.min()
+
+
+def test_exact_set_nearest_neighbour_tie_goes_to_the_smaller_id():
+    """Row 0 shares 2 of its 3 columns with row 1 (4 columns) and 3 with row 2: row 1 wins at 16
+    columns for row 2 (c^2/|B| = 1 against 9/16); at 9 columns both have c^2/|B| = 1, cosines equal
+    as numbers, and the smaller id wins.  A row sharing no column gets the smallest other id."""
+    from oracle import quality
+    rows = [[0, 1, 2], [0, 1, 10, 11], [0, 1, 2, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32],
+            [100]]
+    rp = np.zeros(len(rows) + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.array(r, np.int32) for r in rows])
+    # cos(0,1) = 2/sqrt(3*4), cos(0,2) = 3/sqrt(3*16): c^2/|B| = 4/4 = 1 and 9/16 -> row 1 wins
+    assert quality.nearest_neighbours_of_sets(rp, col, 200, [0]).tolist() == [1]
+    rows[2] = [0, 1, 2, 20, 21, 22, 23, 24, 25]  # c^2/|B| = 9/9 = 1: a tie with row 1
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate([np.array(r, np.int32) for r in rows])
+    assert quality.nearest_neighbours_of_sets(rp, col, 200, [0]).tolist() == [1]
+    assert quality.nearest_neighbours_of_sets(rp, col, 200, [3]).tolist() == [0]  # no shared column
