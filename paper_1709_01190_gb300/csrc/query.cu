@@ -373,7 +373,26 @@ __device__ __forceinline__ uint32_t keys_from_list(const WarpGroup &g, const Reg
 // off[w][i] the element offset such that stream position x of that table is
 // ids[off + x].  Returns M, the number of candidates; misc[9] = the longest
 // stream.
-__device__ uint32_t build_streams(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q) {
+// The head of query q on the block path, thread t < L taking table t: its
+// bucket address, then the bucket's segment [s, e).  Split in two so that the
+// kernel can have the next queries' loads in flight while it counts one.
+__device__ __forceinline__ uint32_t head_key(const QArgs &a, int64_t q) {
+  const uint32_t t = threadIdx.x;
+  return (q >= 0 && q < a.nq && t < a.L) ? query_key(a, q, t) : a.T;
+}
+__device__ __forceinline__ void head_range(const QArgs &a, uint32_t key, uint32_t &s, uint32_t &e) {
+  const uint32_t t = threadIdx.x;
+  s = 0;
+  e = 0;
+  if (t < a.L && key < a.T) {
+    const uint64_t keep = l2_policy_keep();
+    const uint32_t *st = a.starts + static_cast<int64_t>(t) * a.st_stride;
+    s = ld_l2(st + key, keep);
+    e = ld_l2(st + key + 1, keep);
+  }
+}
+
+__device__ uint32_t build_streams(const BlockGroup &g, const QArgs &a, const Region &r, uint32_t s, uint32_t e) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     r.misc[8] = 0;
@@ -381,14 +400,6 @@ __device__ uint32_t build_streams(const BlockGroup &g, const QArgs &a, const Reg
   }
   const uint32_t t = threadIdx.x;  // blockDim >= L: one table per thread
   if (t < a.L) {
-    const uint32_t key = (q >= 0 && q < a.nq) ? query_key(a, q, t) : a.T;
-    uint32_t s = 0, e = 0;
-    if (key < a.T) {
-      const uint64_t keep = l2_policy_keep();
-      const uint32_t *st = a.starts + static_cast<int64_t>(t) * a.st_stride;
-      s = ld_l2(st + key, keep);
-      e = ld_l2(st + key + 1, keep);
-    }
     const uint32_t m = e - s;
     r.mt[t] = m < a.R ? m : a.R;
     r.sbk[t] = s;
@@ -1064,45 +1075,74 @@ __global__ void __launch_bounds__(kQWarps * 32, 3) query_warp_kernel(QArgs a) {
 // Tier 1 takes the queries whose candidates fit a.table_words slots at load
 // below 2/3 and marks the others overflow[h] = -(q + 1) (with all_queries it
 // writes every entry: q or the mark); tier 2 takes exactly the marked ones.
+// The block's next queries are staged while it works on one: the bucket
+// ranges of the next, the addresses of the one after, and the list entry of
+// the third (each load's result is used one iteration later).
 __global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int all_queries, int tier) {
   extern __shared__ uint32_t smem[];
   const BlockGroup g;
   const Region r = carve_big(smem, a);
   const int64_t count = all_queries ? a.nq : static_cast<int64_t>(*a.over_count);
-  for (int64_t h = blockIdx.x; h < count; h += gridDim.x) {
-    int64_t q;
-    if (tier == 1) {
-      q = all_queries ? h : a.overflow[h];
-    } else {
-      const int64_t v = a.overflow[h];
-      if (v >= 0) continue;
-      q = -v - 1;
-    }
-    const uint32_t M = build_streams(g, a, r, q);
-    const uint32_t S = big_table_size(M);
-    const bool defer = tier == 1 && S > a.table_words;
-    if (tier == 1 && threadIdx.x == 0 && (defer || all_queries)) a.overflow[h] = defer ? -q - 1 : q;
-    if (defer) {
-      // left to tier 2
-    } else if (M == 0) {
-      write_empty(g, a, q);
-    } else {
-      const int warp = threadIdx.x >> 5;
-      const uint32_t ntab = a.L > static_cast<uint32_t>(warp) ? (a.L - warp + kBigWarps - 1) / kBigWarps : 0;
-      const uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
-      const uint32_t nbatch = (r.misc[9] + 32 * kBatch - 1) / (32 * kBatch);
-      int32_t ids[kBatch];
-      uint32_t cur = 0;
-      load_stream_ids(a, wp, r.off + warp * kMaxTabPerWarp, wp[ntab], 0, cur, ids);
-      count_phase_block(g, a, r, q, nbatch, ids, cur, S);
-      if (a.k <= 256) {
-        select_from_table(g, a, r, q, S);
+  constexpr int64_t kNone = INT64_MIN;
+  // the list entry of index h (its query in tier 1, the mark tier 1 left in
+  // tier 2), kNone past the end
+  auto entry = [&](int64_t h) -> int64_t {
+    if (h >= count) return kNone;
+    return (all_queries && tier == 1) ? h : a.overflow[h];
+  };
+  // the query an entry stands for in this tier, -1 for none
+  auto query_of = [&](int64_t v) -> int64_t {
+    if (v == kNone) return -1;
+    if (tier == 1) return v;
+    return v < 0 ? -v - 1 : -1;
+  };
+  const int64_t step = gridDim.x;
+  int64_t h = blockIdx.x;
+  int64_t q = query_of(entry(h));
+  uint32_t s_c, e_c;
+  head_range(a, head_key(a, q), s_c, e_c);
+  int64_t qn = query_of(entry(h + step));
+  uint32_t key_n = head_key(a, qn);
+  int64_t raw_n2 = entry(h + 2 * step);
+  for (; h < count; h += step) {
+    uint32_t s_n, e_n;
+    head_range(a, key_n, s_n, e_n);
+    const int64_t qn2 = query_of(raw_n2);
+    const uint32_t key_n2 = head_key(a, qn2);
+    const int64_t raw_n3 = entry(h + 3 * step);
+    if (q >= 0) {
+      const uint32_t M = build_streams(g, a, r, s_c, e_c);
+      const uint32_t S = big_table_size(M);
+      const bool defer = tier == 1 && S > a.table_words;
+      if (tier == 1 && threadIdx.x == 0 && (defer || all_queries)) a.overflow[h] = defer ? -q - 1 : q;
+      if (defer) {
+        // left to tier 2
+      } else if (M == 0) {
+        write_empty(g, a, q);
       } else {
-        const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
-        select_phase(g, a, r, q, r.tab, E);
+        const int warp = threadIdx.x >> 5;
+        const uint32_t ntab = a.L > static_cast<uint32_t>(warp) ? (a.L - warp + kBigWarps - 1) / kBigWarps : 0;
+        const uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
+        const uint32_t nbatch = (r.misc[9] + 32 * kBatch - 1) / (32 * kBatch);
+        int32_t ids[kBatch];
+        uint32_t cur = 0;
+        load_stream_ids(a, wp, r.off + warp * kMaxTabPerWarp, wp[ntab], 0, cur, ids);
+        count_phase_block(g, a, r, q, nbatch, ids, cur, S);
+        if (a.k <= 256) {
+          select_from_table(g, a, r, q, S);
+        } else {
+          const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
+          select_phase(g, a, r, q, r.tab, E);
+        }
       }
+      g.sync();
     }
-    g.sync();
+    q = qn;
+    qn = qn2;
+    s_c = s_n;
+    e_c = e_n;
+    key_n = key_n2;
+    raw_n2 = raw_n3;
   }
 }
 
@@ -1167,12 +1207,16 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
   a.overflow = l.overflow;
   if (cudaMemsetAsync(l.counters, 0, 2 * sizeof(unsigned long long), stream) != cudaSuccess) return FLASH_ECUDA;
 
-  const bool warp_ok = l.k <= 256;
+  // The warp path takes queries of at most tw / 2 candidates.  In the all-points
+  // graph every table's bucket holds the query row itself, so a query has at
+  // least L candidates: with L >= tw / 2 (nearly) every query would only be
+  // passed on to the block path, and the warp kernel is skipped.
+  const uint32_t full_table = next_pow2(2 * l.L * l.R) < 64 ? 64 : next_pow2(2 * l.L * l.R);
+  uint32_t tw = l.warp_table ? l.warp_table : 512u;
+  if (tw > full_table) tw = full_table;
+  const bool warp_ok = l.k <= 256 && !(l.exclude_self && 2 * l.L >= tw);
   int all = 1;
   if (warp_ok) {
-    const uint32_t full_table = next_pow2(2 * l.L * l.R) < 64 ? 64 : next_pow2(2 * l.L * l.R);
-    uint32_t tw = l.warp_table ? l.warp_table : 512u;
-    if (tw > full_table) tw = full_table;
     a.table_words = tw;
     a.region_words = region_words(a);
     while (a.table_words > 64 && static_cast<size_t>(kQWarps) * a.region_words * sizeof(uint32_t) > max_smem_optin()) {

@@ -20,7 +20,8 @@
 //                  coalesced writes of each digit run to scan offset +
 //                  position in the run.
 //      With one pass the scan already holds every segment's start; with more,
-//      a boundary kernel reads them off the partitioned addresses.
+//      the first pass also counts all the high bits per table, and the scan of
+//      that histogram gives the starts.
 //   2. segments: one warp per segment (about n / 2^hb points) counts its 2^lo
 //      low digits in shared memory, scans them, writes the bucket starts of
 //      its 2^lo buckets and lists the buckets holding more than R points, and
@@ -41,8 +42,10 @@ namespace {
 constexpr int kSortWarps = 16;  // per (table, tile) block: 16 warps of 8 ranking rounds (measured against 8 and 32)
 constexpr int kTile = 4096;         // elements per (table, tile) block, histogram and scatter
 constexpr int kMaxBinsSort = 257;   // 8-bit digit + the sentinel value
+constexpr uint32_t kFullSmem = 8193;  // high-bit histograms up to 2^13 + 1 values in shared memory
 constexpr int kLoBits = 10;         // low address bits sorted per segment (2^10 counters per warp)
 constexpr int kSegWarps = 8;        // warps per block of the segment kernel
+constexpr int kSegBatch = 4;        // rounds of 32 points a segment warp has in flight (8 measured slower)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct PassArgs {
@@ -64,19 +67,48 @@ __device__ __forceinline__ uint32_t round_peers(uint32_t *mask, uint32_t d, bool
   return valid ? mask[d] : 0u;
 }
 
+// Per (table, tile) digit histogram of one partition pass.  With FULL (the
+// first of several passes), also the table's histogram of all the high bits
+// (address >> lo, nfull = 2^hb + 1 values with the sentinel), added into
+// full[t][.]: its exclusive scan gives every segment's start, so no later pass
+// has to read the partitioned addresses again to find them.  Without FULL a
+// block takes one tile; with it a few blocks per table walk its tiles, so that
+// the high-bit histogram is added once per block.
+template <bool FULL>
 __global__ void __launch_bounds__(256) radix_hist_kernel(const uint32_t *keys, int64_t n, PassArgs p, uint32_t tile,
-                                                          int64_t tiles, uint32_t *hist) {
+                                                          int64_t tiles, uint32_t *hist, uint32_t *full, uint32_t lo,
+                                                          uint32_t nfull) {
   __shared__ uint32_t h[kMaxBinsSort + 7];
+  extern __shared__ uint32_t hf[];  // [nfull] when FULL and nfull <= kFullSmem
   const uint32_t t = blockIdx.y;
-  const int64_t ti = blockIdx.x;
-  for (int i = threadIdx.x; i < p.nbins; i += blockDim.x) h[i] = 0;
-  __syncthreads();
+  const bool fsm = FULL && nfull <= kFullSmem;
+  if (fsm)
+    for (uint32_t i = threadIdx.x; i < nfull; i += blockDim.x) hf[i] = 0;
   const uint32_t *seg = keys + static_cast<int64_t>(t) * n;
-  const int64_t a = ti * tile, b = min(n, a + static_cast<int64_t>(tile));
-  for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) atomicAdd(&h[digit_of(__ldcs(seg + e), p)], 1u);
-  __syncthreads();
-  for (int i = threadIdx.x; i < p.nbins; i += blockDim.x)
-    hist[(static_cast<int64_t>(t) * p.nbins + i) * tiles + ti] = h[i];
+  uint32_t *ft = FULL ? full + static_cast<int64_t>(t) * nfull : nullptr;
+  for (int64_t ti = blockIdx.x; ti < tiles; ti += FULL ? gridDim.x : tiles) {
+    for (int i = threadIdx.x; i < p.nbins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t a = ti * tile, b = min(n, a + static_cast<int64_t>(tile));
+    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+      const uint32_t key = __ldcs(seg + e);
+      atomicAdd(&h[digit_of(key, p)], 1u);
+      if (FULL) {
+        if (fsm)
+          atomicAdd(&hf[key >> lo], 1u);
+        else
+          atomicAdd(&ft[key >> lo], 1u);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.nbins; i += blockDim.x)
+      hist[(static_cast<int64_t>(t) * p.nbins + i) * tiles + ti] = h[i];
+  }
+  if (fsm) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nfull; i += blockDim.x)
+      if (hf[i]) atomicAdd(&ft[i], hf[i]);
+  }
 }
 
 // exclusive scan of hist[t][0..len) in place, one block per table
@@ -259,45 +291,6 @@ size_t scatter_smem_bytes(int nb_pad) {
   return sizeof(uint32_t) * (2 * kTile + (2 * kSortWarps + 2) * static_cast<size_t>(nb_pad));
 }
 
-// Segment starts after a multi-pass partition: seg[t][s] = number of
-// addresses a of table t with (a >> shift) < s, for s in [0, S]; the addresses
-// are sorted by a >> shift, so each change of that value writes the starts of
-// the values it skips (a short run by its own thread, a long one by the warp).
-__global__ void __launch_bounds__(256) segment_starts_kernel(const uint32_t *skeys, int64_t n, uint32_t shift,
-                                                              uint32_t S, uint32_t *seg_starts) {
-  const uint32_t t = blockIdx.y;
-  const uint32_t *seg = skeys + static_cast<int64_t>(t) * n;
-  uint32_t *st = seg_starts + static_cast<int64_t>(t) * (static_cast<int64_t>(S) + 1);
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nn = static_cast<uint32_t>(n);
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base <= nn; base += stride) {
-    const uint32_t i = base + lane;
-    const uint32_t kc = i < nn ? (seg[i] >> shift) : S + 1;  // past the end: above every value
-    uint32_t kp = __shfl_up_sync(kFull, kc, 1);
-    if (lane == 0) kp = base > 0 ? (seg[base - 1] >> shift) : 0xFFFFFFFFu;  // none before the first element
-    // values kp + 1 .. min(kc, S) start at i (kp + 1 wraps to 0 for the first element)
-    uint32_t lo = 1, hi = 0;
-    if (i <= nn) {
-      lo = kp + 1;
-      hi = kc < S ? kc : S;
-    }
-    if (lo <= hi && hi - lo < 8) {
-      for (uint32_t v = lo; v <= hi; ++v) st[v] = i;
-      lo = 1;
-      hi = 0;
-    }
-    uint32_t m = __ballot_sync(kFull, lo <= hi);
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1;
-      const uint32_t glo = __shfl_sync(kFull, lo, src), ghi = __shfl_sync(kFull, hi, src);
-      const uint32_t gi = __shfl_sync(kFull, i, src);
-      for (uint32_t v = glo + lane; v <= ghi; v += 32) st[v] = gi;
-    }
-  }
-}
-
 __host__ __device__ __forceinline__ uint32_t cpad(uint32_t d) { return d + (d >> 5); }
 __host__ __device__ __forceinline__ uint32_t seg_counter_words(uint32_t lo) {
   return cpad(1u << lo) + 1u;
@@ -361,25 +354,26 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
       msk[d] = 0;
     }
     __syncwarp();
-    // count the low digits (the next 128 addresses are loaded while 128 are counted)
+    // count the low digits (the next kSegBatch * 32 addresses are loaded while as
+    // many are counted)
     {
-      uint32_t k[4], kn[4];
+      uint32_t k[kSegBatch], kn[kSegBatch];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < kSegBatch; ++r) {
         const uint32_t i = so + r * 32 + lane;
         k[r] = i < se ? pk[i] : 0xFFFFFFFFu;
       }
-      for (uint32_t base = so; base < se; base += 128) {
+      for (uint32_t base = so; base < se; base += kSegBatch * 32) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const uint32_t i = base + 128 + r * 32 + lane;
+        for (int r = 0; r < kSegBatch; ++r) {
+          const uint32_t i = base + kSegBatch * 32 + r * 32 + lane;
           kn[r] = i < se ? pk[i] : 0xFFFFFFFFu;
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < kSegBatch; ++r)
           if (k[r] != 0xFFFFFFFFu) atomicAdd(&cnt[cpad(k[r] & dmask)], 1u);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) k[r] = kn[r];
+        for (int r = 0; r < kSegBatch; ++r) k[r] = kn[r];
       }
     }
     // exclusive scan in place (lane owns a run of consecutive digits); heavy buckets
@@ -413,26 +407,26 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
     for (uint32_t d = lane; d < nb; d += 32) st_l2(st + ((s << a.lo) | d), cnt[cpad(d)], keep);
     __syncwarp();
     // place: rank among equal digits of the round, after the earlier rounds
-    // (the next 128 points are loaded while 128 are placed)
-    uint32_t kk[4];
-    int32_t id[4];
+    // (the next kSegBatch * 32 points are loaded while as many are placed)
+    uint32_t kk[kSegBatch];
+    int32_t id[kSegBatch];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < kSegBatch; ++r) {
       const uint32_t i = so + r * 32 + lane;
       kk[r] = i < se ? pk[i] : 0u;
       id[r] = i < se ? pi[i] : 0;
     }
-    for (uint32_t base = so; base < se; base += 128) {
-      uint32_t kn[4];
-      int32_t idn[4];
+    for (uint32_t base = so; base < se; base += kSegBatch * 32) {
+      uint32_t kn[kSegBatch];
+      int32_t idn[kSegBatch];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const uint32_t i = base + 128 + r * 32 + lane;
+      for (int r = 0; r < kSegBatch; ++r) {
+        const uint32_t i = base + kSegBatch * 32 + r * 32 + lane;
         kn[r] = i < se ? pk[i] : 0u;
         idn[r] = i < se ? pi[i] : 0;
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < kSegBatch; ++r) {
         const uint32_t i = base + r * 32 + lane;
         if (base + r * 32 < se) {  // warp-uniform
           const bool valid = i < se;
@@ -449,7 +443,7 @@ __global__ void __launch_bounds__(kSegWarps * 32) segment_sort_kernel(SegArgs a)
         }
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < kSegBatch; ++r) {
         kk[r] = kn[r];
         id[r] = idn[r];
       }
@@ -491,11 +485,27 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
   const dim3 grid(static_cast<unsigned>(plan.tiles), s.L);
   const uint32_t *kin = s.keys_in;
   const int32_t *vin = nullptr;
+  const uint32_t S = 1u << plan.hi_bits;
+  if (plan.passes > 1 &&
+      cudaMemsetAsync(s.seg, 0, sizeof(uint32_t) * s.L * (static_cast<size_t>(S) + 1), stream) != cudaSuccess)
+    return FLASH_ECUDA;
   for (int pass = 0; pass < plan.passes; ++pass) {
     PassArgs pa{plan.shift[pass], plan.bits[pass], plan.nbins[pass], pass == plan.passes - 1};
     uint32_t *kout = pass % 2 == 0 ? s.tmp_keys : s.keys_out;
     int32_t *vout = pass % 2 == 0 ? s.tmp_ids : s.tmp_ids2;
-    radix_hist_kernel<<<grid, 256, 0, stream>>>(kin, s.n, pa, plan.tile, plan.tiles, s.hist);
+    uint32_t *full = (plan.passes > 1 && pass == 0) ? s.seg : nullptr;
+    const size_t hsm = full && S + 1 <= kFullSmem ? sizeof(uint32_t) * (S + 1) : 0;
+    // with the high-bit histogram, a few blocks per table walk its tiles (the histogram is
+    // added once per block); otherwise a block per tile
+    if (full) {
+      int64_t hx = (16LL * num_sms() + s.L - 1) / s.L;
+      if (hx > plan.tiles) hx = plan.tiles;
+      if (hx < 1) hx = 1;
+      radix_hist_kernel<true><<<dim3(static_cast<unsigned>(hx), s.L), 256, hsm, stream>>>(
+          kin, s.n, pa, plan.tile, plan.tiles, s.hist, full, static_cast<uint32_t>(plan.lo_bits), S + 1);
+    } else {
+      radix_hist_kernel<false><<<grid, 256, 0, stream>>>(kin, s.n, pa, plan.tile, plan.tiles, s.hist, nullptr, 0, 0);
+    }
     radix_scan_kernel<<<s.L, 1024, 0, stream>>>(s.hist, static_cast<int64_t>(pa.nbins) * plan.tiles);
     const int nb_pad = (pa.nbins + 3) & ~3;
     const size_t smem = scatter_smem_bytes(nb_pad);
@@ -516,15 +526,13 @@ int sort_tables(const SortPlan &plan, const SortLaunch &s, cudaStream_t stream) 
   a.L = s.L;
   a.lo = static_cast<uint32_t>(plan.lo_bits);
   a.hb = static_cast<uint32_t>(plan.hi_bits);
-  const uint32_t S = 1u << plan.hi_bits;
   if (plan.passes == 1) {
     a.seg = s.hist;
     a.seg_tstride = static_cast<int64_t>(plan.nbins[0]) * plan.tiles;
     a.seg_sstride = plan.tiles;
   } else {
-    const int64_t blocks_x = (s.n + 1 + 255) / 256;
-    const dim3 g2(static_cast<unsigned>(blocks_x < 1024 ? blocks_x : 1024), s.L);
-    segment_starts_kernel<<<g2, 256, 0, stream>>>(kin, s.n, static_cast<uint32_t>(plan.lo_bits), S, s.seg);
+    // segment starts: exclusive scan of the high-bit histogram the first pass counted
+    radix_scan_kernel<<<s.L, 1024, 0, stream>>>(s.seg, static_cast<int64_t>(S) + 1);
     count_launches(1);
     a.seg = s.seg;
     a.seg_tstride = static_cast<int64_t>(S) + 1;
