@@ -540,22 +540,35 @@ __global__ void __launch_bounds__(256) row_class_scatter_kernel(const int64_t *r
 }
 
 // 32 x 32 tiles (rows x tables): coalesced reads along the tables of a row,
-// coalesced writes along the rows of a table.
+// coalesced writes along the rows of a table.  A grid of a few blocks per SM
+// walks the tiles (one tile per block would make millions of tiny blocks at
+// L = 256); each thread has its four loads in flight before it stores.
 __global__ void __launch_bounds__(256) transpose_keys_kernel(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *tm,
                                                               int64_t ld) {
   __shared__ uint32_t tile[32][33];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;  // rows on x (up to 2^31 - 1 blocks)
-  const uint32_t t0 = blockIdx.y * 32;
-  for (uint32_t y = threadIdx.y; y < 32; y += 8) {
-    const int64_t r = r0 + y;
-    const uint32_t t = t0 + threadIdx.x;
-    if (r < n && t < L) tile[y][threadIdx.x] = __ldcs(rm + r * L + t);
-  }
-  __syncthreads();
-  for (uint32_t y = threadIdx.y; y < 32; y += 8) {
-    const uint32_t t = t0 + y;
-    const int64_t r = r0 + threadIdx.x;
-    if (r < n && t < L) tm[static_cast<int64_t>(t) * ld + r] = tile[threadIdx.x][y];
+  const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t row_tiles = (n + 31) / 32;
+  const int64_t tiles = row_tiles * ((L + 31) / 32);
+  for (int64_t ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
+    const int64_t r0 = (ti % row_tiles) * 32;
+    const uint32_t t0 = static_cast<uint32_t>(ti / row_tiles) * 32;
+    uint32_t v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + ty + 8 * i;
+      const uint32_t t = t0 + tx;
+      v[i] = (r < n && t < L) ? __ldcs(rm + r * L + t) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tile[ty + 8 * i][tx] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t t = t0 + ty + 8 * i;
+      const int64_t r = r0 + tx;
+      if (r < n && t < L) tm[static_cast<int64_t>(t) * ld + r] = tile[tx][ty + 8 * i];
+    }
+    __syncthreads();
   }
 }
 
@@ -563,8 +576,10 @@ __global__ void __launch_bounds__(256) transpose_keys_kernel(const uint32_t *rm,
 
 int launch_transpose_keys(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *tm, int64_t ld, cudaStream_t stream) {
   if (n <= 0) return 0;
-  const dim3 grid(static_cast<unsigned>((n + 31) / 32), (L + 31) / 32);
-  transpose_keys_kernel<<<grid, dim3(32, 8), 0, stream>>>(rm, n, L, tm, ld);
+  const int64_t tiles = ((n + 31) / 32) * ((L + 31) / 32);
+  int64_t blocks = 8LL * num_sms();
+  if (blocks > tiles) blocks = tiles;
+  transpose_keys_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(rm, n, L, tm, ld);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }

@@ -10,20 +10,22 @@
 //            (id + 1) << 8 | (count - 1) (id < 2^24 - 1, count <= L <= 256),
 //            inserted with atomicCAS and incremented with atomicAdd; each new
 //            entry's slot is appended to a list.  Block path (thousands of
-//            candidates, nearly all distinct): returning shared atomics (CAS,
-//            OR) have a small fraction of the throughput of non-returning
-//            ones (red) on this part, so tags id + 1 are placed in
-//            barrier-separated rounds instead: a read step probes to the
+//            candidates, nearly all distinct): tags id + 1 in one array,
+//            16-bit counts in a parallel one (added with red).  A query whose
+//            warps' candidate streams take one or two batches places its tags
+//            by atomicCAS; with more batches returning shared atomics cost
+//            more than barrier-separated rounds: a read step probes to the
 //            id's slot or to the first empty one, a write step stores the tag
 //            into that empty slot (blind; the last writer wins) and the next
-//            read step finds whether this id won.  Counts go to a parallel
-//            array of 16-bit counters through red; the few ids still unplaced
-//            after the last round use atomicCAS.  The table is then
-//            compacted in place into sort keys;
+//            read step finds whether this id won (on the empty table of the
+//            first batch every id goes straight to its home slot); the few
+//            ids still unplaced after the last round use atomicCAS;
 //   select : the k largest sort keys (count - 1) << 24 | (2^24 - 1 - id),
 //            i.e. count descending then id ascending, found by a radix select
-//            over 8-bit digits (histogram, suffix sum, threshold), collected
-//            and bitonic-sorted.  The excluded id is never inserted.
+//            over 8-bit digits (histogram, suffix sum, threshold) and
+//            collected; the warp path bitonic-sorts them, the block path
+//            writes each at its rank (the number of larger keys).  The
+//            excluded id is never inserted.
 // This replaces the paper's segmented sort + CountReduce on the GPU
 // (Section 3.4.1) by one pass through shared memory; the result is the
 // unique top-k of the (count desc, id asc) order, identical to sorting.
@@ -104,8 +106,9 @@ struct Region {
   uint32_t *tab, *aux, *pre[2], *sb[2], *hist, *sel, *misc;
   // block path only: per-table reservoir sizes and segment starts, each
   // warp's candidate stream (table starts in the stream, element offsets),
-  // and the list of keys gathered by the selection
-  uint32_t *mt, *sbk, *wpre, *lst;
+  // the list of keys gathered by the selection, and the bitmap of slots whose
+  // id arrived more than once (one bit per table slot)
+  uint32_t *mt, *sbk, *wpre, *lst, *dup;
   long long *off;
 };
 
@@ -129,8 +132,8 @@ __device__ __forceinline__ Region carve(uint32_t *base, const QArgs &a) {
   return r;
 }
 
-// Block path: [tab S][aux S/2][mt 256][sbk 256][wpre 16x17 (+pad)][off 16x16 x2][lst 2048][hist 256][sel kp]
-//             [misc 40]
+// Block path: [tab S][aux S/2][mt 256][sbk 256][wpre 16x17 (+pad)][off 16x16 x2][lst 2048][dup S/32]
+//             [hist 256][sel kp][misc 40]
 constexpr uint32_t kWpreWords = (kBigWarps * (kMaxTabPerWarp + 1) + 3) & ~3u;
 
 __device__ __forceinline__ Region carve_big(uint32_t *base, const QArgs &a) {
@@ -142,7 +145,8 @@ __device__ __forceinline__ Region carve_big(uint32_t *base, const QArgs &a) {
   r.wpre = r.sbk + 256;
   r.off = reinterpret_cast<long long *>(r.wpre + kWpreWords);
   r.lst = reinterpret_cast<uint32_t *>(r.off + kBigWarps * kMaxTabPerWarp);
-  r.hist = r.lst + kListCap;
+  r.dup = r.lst + kListCap;
+  r.hist = r.dup + (a.table_words + 31) / 32;
   r.sel = r.hist + 256;
   r.misc = r.sel + a.kp;
   return r;
@@ -150,7 +154,7 @@ __device__ __forceinline__ Region carve_big(uint32_t *base, const QArgs &a) {
 
 uint32_t big_region_words(const QArgs &a) {
   const uint32_t w = a.table_words + a.table_words / 2 + 512 + kWpreWords + 2 * kBigWarps * kMaxTabPerWarp + kListCap +
-                     256 + a.kp + 40;
+                     (a.table_words + 31) / 32 + 256 + a.kp + 40;
   return (w + 3) & ~3u;
 }
 
@@ -465,7 +469,7 @@ __device__ __forceinline__ void count_add(uint32_t *cnt, uint32_t h) {
 // race shows up in the next read step.  Ids still unplaced after kRounds
 // rounds are inserted with atomicCAS once the block's writes are done.
 __device__ __forceinline__ void count_batch(const BlockGroup &g, const Region &r, uint32_t S, uint32_t lg,
-                                            const int32_t (&idv)[kBatch], int32_t excl) {
+                                            const int32_t (&idv)[kBatch], int32_t excl, bool fresh) {
   constexpr int kRounds = 3;
   uint32_t h[kBatch];
   uint32_t pend = 0;
@@ -481,6 +485,19 @@ __device__ __forceinline__ void count_batch(const BlockGroup &g, const Region &r
   bool done = false;
   for (int round = 0; round < kRounds; ++round) {
     uint32_t want = 0;
+    if (round == 0 && fresh) {
+      // the table is empty: the read step would find every home slot empty
+      want = pend;
+      if (!__syncthreads_or(want != 0)) {
+        done = true;
+        break;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j)
+        if ((want >> j) & 1u) r.tab[h[j]] = static_cast<uint32_t>(idv[j]) + 1u;
+      g.sync();
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
       if ((pend >> j) & 1u) {
@@ -528,6 +545,37 @@ __device__ __forceinline__ void count_batch(const BlockGroup &g, const Region &r
   }
 }
 
+// COUNTFREQUENCY of one batch by atomicCAS inserts (linear probing, no
+// rounds): for a query of one or two batches (up to 512 ids in a warp's
+// stream) this beats the barrier-separated rounds, whose three read/write
+// passes per batch cost more than the returning atomics; with more batches
+// the rounds win (measured on kdd12-like and url-like queries).
+// An insert that finds its id already present marks the slot in r.dup; `fresh`
+// counts this thread's new entries.
+__device__ __forceinline__ void count_batch_cas(const Region &r, uint32_t S, uint32_t lg,
+                                                const int32_t (&idv)[kBatch], int32_t excl, uint32_t &fresh) {
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    if (idv[j] >= 0 && idv[j] != excl) {
+      const uint32_t tag = static_cast<uint32_t>(idv[j]) + 1u;
+      uint32_t h = slot_hash(idv[j], lg);
+      for (;;) {
+        uint32_t w = r.tab[h];
+        if (w == 0) w = atomicCAS(&r.tab[h], 0u, tag);
+        if (w == 0 || w == tag) {
+          count_add(r.aux, h);
+          if (w == 0)
+            ++fresh;
+          else
+            atomicOr(&r.dup[h >> 5], 1u << (h & 31u));
+          break;
+        }
+        h = (h + 1) & (S - 1);
+      }
+    }
+  }
+}
+
 // COUNTFREQUENCY of the block path into a table of S slots (tags in tab,
 // counts in aux), over nbatch batches of each warp's stream.  The first batch
 // of ids is given (loaded ahead by the caller); later batches are loaded here.
@@ -546,10 +594,24 @@ __device__ void count_phase_block(const BlockGroup &g, const QArgs &a, const Reg
   int32_t idv[kBatch];
 #pragma unroll
   for (int j = 0; j < kBatch; ++j) idv[j] = first[j];
-  for (uint32_t b = 0;;) {
-    count_batch(g, r, S, lg, idv, excl);
-    if (++b >= nbatch) break;
-    load_stream_ids(a, wp, of, len, b * 32 * kBatch, cur, idv);
+  if (nbatch <= 2) {
+    for (uint32_t i = g.rank(); i < S / 32; i += g.size()) r.dup[i] = 0;
+    if (g.rank() == 0) r.misc[10] = 0;
+    g.sync();  // the cleared table is visible
+    uint32_t fresh = 0;
+    for (uint32_t b = 0;;) {
+      count_batch_cas(r, S, lg, idv, excl, fresh);
+      if (++b >= nbatch) break;
+      load_stream_ids(a, wp, of, len, b * 32 * kBatch, cur, idv);
+    }
+    fresh = __reduce_add_sync(kFull, fresh);
+    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(&r.misc[10], fresh);
+  } else {
+    for (uint32_t b = 0;;) {
+      count_batch(g, r, S, lg, idv, excl, b == 0);
+      if (++b >= nbatch) break;
+      load_stream_ids(a, wp, of, len, b * 32 * kBatch, cur, idv);
+    }
   }
   g.sync();
 }
@@ -624,6 +686,32 @@ __device__ __forceinline__ void warp_sort_winners(const QArgs &a, const uint32_t
   else if (nsel <= 64) warp_sort_and_write<2>(a, sel, nsel, q);
   else if (nsel <= 128) warp_sort_and_write<4>(a, sel, nsel, q);
   else warp_sort_and_write<8>(a, sel, nsel, q);
+}
+
+// nsel <= 256 distinct winners written in descending order by the block:
+// winner i goes to position rank(i) = the number of winners larger than it,
+// counted by P threads (the largest power of two <= 32 with P * nsel <= the
+// block size) and summed over them with shuffles.  Positions nsel .. k - 1 are
+// padded.
+__device__ __forceinline__ void block_rank_write(const QArgs &a, const uint32_t *sel, uint32_t nsel, int64_t q) {
+  uint32_t lp = 5;  // log2 P
+  while (lp > 0 && (nsel << lp) > kBigThreads) --lp;
+  const uint32_t t = threadIdx.x, P = 1u << lp;
+  const uint32_t i = t >> lp, part = t & (P - 1);
+  uint32_t key = 0, above = 0;
+  if (i < nsel) {
+    key = sel[i];
+    for (uint32_t j = part; j < nsel; j += P) above += sel[j] > key ? 1u : 0u;
+  }
+  for (uint32_t o = 1; o < P; o <<= 1) above += __shfl_xor_sync(kFull, above, o);
+  if (i < nsel && part == 0 && above < static_cast<uint32_t>(a.k)) {
+    __stcs(a.out_ids + q * a.k + above, static_cast<int32_t>(0xFFFFFFu - (key & 0xFFFFFFu)));
+    __stcs(a.out_counts + q * a.k + above, static_cast<int32_t>((key >> 24) + 1u));
+  }
+  for (uint32_t j = nsel + t; j < static_cast<uint32_t>(a.k); j += kBigThreads) {
+    __stcs(a.out_ids + q * a.k + j, -1);
+    __stcs(a.out_counts + q * a.k + j, 0);
+  }
 }
 
 // nsel winners sorted by the block (bitonic network over kp slots in shared memory).
@@ -863,7 +951,8 @@ __device__ __forceinline__ void for_table_keys(const Region &r, uint32_t S, F &&
 // passes read that list when the threshold count is >= 2 and the list is
 // complete; otherwise they read the table, and the keys reaching the
 // threshold are gathered into the list once there are at most kListCap.
-__device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q, uint32_t S) {
+__device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q, uint32_t S,
+                                  bool dup_known) {
   // misc: [0] prefix [1] pmask [2] need [3] stop [4] threshold [5] gathered [6] keys >= threshold
   //       [7] keys above the prefix range
   uint32_t *misc = r.misc;
@@ -883,7 +972,41 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
     for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
     g.sync();
     const uint32_t prefix = misc[0], pmask = misc[1];
-    if (pass == 0) {
+    if (pass == 0 && dup_known) {
+      // the count >= 2 entries are the slots marked in r.dup: their keys go to
+      // the list (one position per warp and round) and their counts to hist;
+      // the count-1 entries are the others, misc[10] - (marked slots)
+      const uint32_t nw = S / 32;
+      for (uint32_t w0 = 0; w0 < nw; w0 += kBigThreads) {
+        const uint32_t w = w0 + threadIdx.x;
+        uint32_t m = w < nw ? r.dup[w] : 0u;
+        const uint32_t nb = __popc(m);
+        uint32_t inc = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t x = __shfl_up_sync(kFull, inc, o);
+          if (lane >= o) inc += x;
+        }
+        uint32_t pos = 0;
+        if (lane == 31 && inc) pos = atomicAdd(&misc[5], inc);
+        pos = __shfl_sync(kFull, pos, 31) + inc - nb;
+        uint32_t twos = 0;
+        for (; m; m &= m - 1u) {
+          const uint32_t slot = 32u * w + static_cast<uint32_t>(__ffs(m) - 1);
+          const uint32_t c = (r.aux[slot >> 1] >> ((slot & 1u) << 4)) & 0xFFFFu;
+          if (pos < kListCap) r.lst[pos] = sort_key(r.tab[slot], c);
+          ++pos;
+          if (c == 2)
+            ++twos;
+          else
+            atomicAdd(&r.hist[c - 1], 1u);
+        }
+        twos = __reduce_add_sync(kFull, twos);
+        if (lane == 0 && twos) atomicAdd(&r.hist[1], twos);
+      }
+      g.sync();
+      if (g.rank() == 0) r.hist[0] += misc[10] - misc[5];
+    } else if (pass == 0) {
       uint32_t ones = 0;
       for (uint32_t base = 0; base < S; base += 4 * kBigThreads) {
         const uint32_t i = base + 4 * threadIdx.x;
@@ -895,12 +1018,37 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
         }
         const uint32_t t[4] = {e.x, e.y, e.z, e.w};
         const uint32_t c[4] = {c2.x & 0xFFFFu, c2.x >> 16, c2.y & 0xFFFFu, c2.y >> 16};
+        uint32_t nm = 0, twos = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const bool multi = t[u] != 0 && c[u] > 1;
           if (t[u] != 0 && c[u] == 1) ++ones;
-          if (multi) atomicAdd(&r.hist[c[u] - 1], 1u);
-          append_warp(r.lst, kListCap, &misc[5], multi, multi ? sort_key(t[u], c[u]) : 0u);
+          if (t[u] != 0 && c[u] > 1) ++nm;
+          if (t[u] != 0 && c[u] == 2) ++twos;
+        }
+        if (__any_sync(kFull, nm != 0)) {
+          // the lanes' count >= 2 entries go to the list at one position per
+          // warp and round (an exclusive scan of nm); count-2 entries, the
+          // common ones, are summed over the warp before they reach hist
+          uint32_t inc = nm;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += x;
+          }
+          uint32_t pos = 0;
+          if (lane == 31) pos = atomicAdd(&misc[5], inc);
+          pos = __shfl_sync(kFull, pos, 31) + inc - nm;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (t[u] != 0 && c[u] > 1) {
+              if (pos < kListCap) r.lst[pos] = sort_key(t[u], c[u]);
+              ++pos;
+              if (c[u] > 2) atomicAdd(&r.hist[c[u] - 1], 1u);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) twos += __shfl_xor_sync(kFull, twos, o);
+          if (lane == 0 && twos) atomicAdd(&r.hist[1], twos);
         }
       }
 #pragma unroll
@@ -997,7 +1145,7 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
     });
   }
   g.sync();
-  if (threadIdx.x < 32) warp_sort_winners(a, r.hist, nsel, q);
+  block_rank_write(a, r.hist, nsel, q);
   g.sync();
 }
 
@@ -1129,7 +1277,7 @@ __global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int 
         load_stream_ids(a, wp, r.off + warp * kMaxTabPerWarp, wp[ntab], 0, cur, ids);
         count_phase_block(g, a, r, q, nbatch, ids, cur, S);
         if (a.k <= 256) {
-          select_from_table(g, a, r, q, S);
+          select_from_table(g, a, r, q, S, nbatch <= 2);
         } else {
           const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
           select_phase(g, a, r, q, r.tab, E);
