@@ -62,6 +62,15 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_max(value: float, dist_mod, device) -> float:
+    """The largest of a per-rank value over all replicas (the slowest rank's time): every rank
+    calls it with its own value and gets the maximum back."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(args, rank):
     from paper_1709_01190_gb300 import synth
     w = synth.WORKLOADS[args.workload]
@@ -602,9 +611,7 @@ def main():
     launches_per_step = fl.flash_last_launch_count()
     clocks = sampler.stop() if sampler else None
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = replica_max(ms, dist, "cuda")
     value = world * n / (ms / 1000.0)
 
     # per-phase device times (same kernels, same launches; events on the stream between phases)
@@ -703,9 +710,7 @@ def main():
             fl.flash_knn_graph_host(params, rp_np, col_np, csr.dim, k, out_i, out_c, stream)
         e2e_s = (time.perf_counter() - t) / args.steps
         if world > 1:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+            e2e_s = replica_max(e2e_s, dist, "cuda")
         link = pinned_copy_ceiling()
         e2e = {"value": world * n / e2e_s, "unit": "queries/s", "ms_per_step": e2e_s * 1000.0,
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * n * k,
