@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--impl", choices=["flash", "reference"], default="flash")
     ap.add_argument("--workload", default="webspam_like")
     ap.add_argument("--rows", type=int, default=0, help="fewer rows (smoke runs only; the line says so)")
+    ap.add_argument("--range-bits", type=int, default=0,
+                    help="override the workload's range bits, e.g. to keep the full-size bucket load on fewer "
+                         "rows for a profile (the line says so)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
@@ -76,6 +79,9 @@ def workload(args, rank):
     w = synth.WORKLOADS[args.workload]
     if args.rows:
         w = w.scaled(args.rows)
+    if getattr(args, "range_bits", 0):
+        w = w.__class__(**{**w.__dict__, "params": w.params.__class__(**{**w.params.__dict__,
+                                                                          "range_bits": args.range_bits})})
     if rank:
         w = w.__class__(**{**w.__dict__, "data": w.data.replace(seed=w.data.seed + 1000 * rank)})
     return w
@@ -647,7 +653,7 @@ def main():
                 "overhead": "a row-major copy of the keys for the graph's queries (4 L N written), not counted",
                 "traffic": None, "duration_ms": hash_phase_ms}
     prof = os.path.join(ROOT, "profiles", "doph_keys_webspam_like_traffic.json")
-    if os.path.exists(prof) and not args.rows and args.workload == "webspam_like":
+    if os.path.exists(prof) and not args.rows and not args.range_bits and args.workload == "webspam_like":
         try:
             import hashlib
             with open(prof) as fh:
@@ -682,7 +688,7 @@ def main():
 
     # the two densifications (rotation; optimal, [36]) on sparse kdd12-like rows, where most bins are empty
     densify = None
-    if not args.rows and args.workload == "webspam_like":
+    if not args.rows and not args.range_bits and args.workload == "webspam_like":
         from paper_1709_01190_gb300 import synth as _s
         wk = _s.WORKLOADS["kdd12_like"].scaled(1_000_000)
         ck = _s.generate(wk.data)
@@ -721,7 +727,7 @@ def main():
                                                 8 * n * k / (link["d2h_GB/s"] * 1e9))) / (e2e_s * 1000.0)}}
 
     config3 = served = config4 = None
-    if rank == 0 and world == 1 and not args.rows:
+    if rank == 0 and world == 1 and not args.rows and not args.range_bits:
         del dev, keys_out, hashes_out
         torch.cuda.empty_cache()
         if not args.no_url:
@@ -742,7 +748,7 @@ def main():
                 "phases_ms": acc, "doph": doph, "plain": plain, "densify": densify, "quality": quality,
                 "graph_replay_ms_per_step": graph_ms, "tuning": tuned,
                 "config3_url_like_batch": config3, "config4_kdd12_like_graph": config4,
-                "served": served, "reduced": bool(args.rows)}
+                "served": served, "reduced": bool(args.rows or args.range_bits)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

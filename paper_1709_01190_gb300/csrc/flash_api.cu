@@ -80,11 +80,13 @@ flash_tuning current_tuning() {
 
 // One stream-ordered allocation carved into 256-byte aligned parts.
 // Scratch comes from a stream-ordered pool per device owned by the library,
-// which keeps up to kPoolKeepBytes reserved between calls: the device's
-// default pool gives memory back at every synchronization, so each call would
-// map its scratch again before its first kernel.  Under stream capture the
-// default pool is used (graph allocations come from the graph's own memory).
-constexpr uint64_t kPoolKeepBytes = 16ull << 30;
+// which keeps up to a quarter of the device's memory (at least 16 GiB)
+// reserved between calls: the device's default pool gives memory back at every
+// synchronization, so each call would map its scratch again before its first
+// kernel (a 10M-row, L = 256 graph needs about 50 GB of scratch; mapping it
+// again cost each call about 50 ms).  Under stream capture the default pool is
+// used (graph allocations come from the graph's own memory).
+constexpr uint64_t kPoolKeepMin = 16ull << 30;
 
 cudaMemPool_t scratch_pool() {
   static std::mutex mu;
@@ -103,7 +105,12 @@ cudaMemPool_t scratch_pool() {
     cudaGetLastError();
     pool = nullptr;
   } else {
-    uint64_t keep = kPoolKeepBytes;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      total_b = 0;
+    }
+    uint64_t keep = total_b / 4 > kPoolKeepMin ? total_b / 4 : kPoolKeepMin;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   pools[d] = pool;
