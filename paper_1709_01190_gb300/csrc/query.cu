@@ -585,6 +585,19 @@ __device__ void count_phase_block(const BlockGroup &g, const QArgs &a, const Reg
   const uint4 z = make_uint4(0u, 0u, 0u, 0u);
   for (uint32_t i = 4 * g.rank(); i < S; i += 4 * g.size()) *reinterpret_cast<uint4 *>(r.tab + i) = z;
   for (uint32_t i = 4 * g.rank(); i < S / 2; i += 4 * g.size()) *reinterpret_cast<uint4 *>(r.aux + i) = z;
+  // the selection's histogram and counters start here, so that it needs no
+  // barrier of its own before its first pass
+  for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
+  if (g.rank() == 0) {
+    r.misc[0] = 0;  // prefix
+    r.misc[1] = 0;  // prefix mask
+    r.misc[2] = static_cast<uint32_t>(a.k);  // keys still needed
+    r.misc[3] = 0;  // stop
+    r.misc[5] = 0;  // keys gathered into the list
+    r.misc[7] = 0;  // keys above the prefix range
+    r.misc[10] = 0;  // new entries (CAS count)
+    r.misc[11] = 0;  // winners gathered
+  }
   const int32_t excl = a.exclude_self ? static_cast<int32_t>(q) : (a.exclude ? a.exclude[q] : -1);
   const int warp = threadIdx.x >> 5;
   const uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
@@ -596,7 +609,6 @@ __device__ void count_phase_block(const BlockGroup &g, const QArgs &a, const Reg
   for (int j = 0; j < kBatch; ++j) idv[j] = first[j];
   if (nbatch <= 2) {
     for (uint32_t i = g.rank(); i < S / 32; i += g.size()) r.dup[i] = 0;
-    if (g.rank() == 0) r.misc[10] = 0;
     g.sync();  // the cleared table is visible
     uint32_t fresh = 0;
     for (uint32_t b = 0;;) {
@@ -954,23 +966,18 @@ __device__ __forceinline__ void for_table_keys(const Region &r, uint32_t S, F &&
 __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Region &r, int64_t q, uint32_t S,
                                   bool dup_known) {
   // misc: [0] prefix [1] pmask [2] need [3] stop [4] threshold [5] gathered [6] keys >= threshold
-  //       [7] keys above the prefix range
+  //       [7] keys above the prefix range [10] new entries (CAS count) [11] winners gathered;
+  // [0] .. [3], [5], [7], [10], [11] and hist were set by count_phase_block before its last barrier
   uint32_t *misc = r.misc;
   const int lane = threadIdx.x & 31;
-  if (g.rank() == 0) {
-    misc[0] = 0;
-    misc[1] = 0;
-    misc[2] = static_cast<uint32_t>(a.k);
-    misc[3] = 0;
-    misc[5] = 0;
-    misc[7] = 0;
-  }
   bool listed = false;
   uint32_t nlist = 0;
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 24 - 8 * pass;
-    for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
-    g.sync();
+    if (pass > 0) {
+      for (uint32_t i = g.rank(); i < 256; i += g.size()) r.hist[i] = 0;
+      g.sync();
+    }
     const uint32_t prefix = misc[0], pmask = misc[1];
     if (pass == 0 && dup_known) {
       // the count >= 2 entries are the slots marked in r.dup: their keys go to
@@ -1004,8 +1011,6 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
         twos = __reduce_add_sync(kFull, twos);
         if (lane == 0 && twos) atomicAdd(&r.hist[1], twos);
       }
-      g.sync();
-      if (g.rank() == 0) r.hist[0] += misc[10] - misc[5];
     } else if (pass == 0) {
       uint32_t ones = 0;
       for (uint32_t base = 0; base < S; base += 4 * kBigThreads) {
@@ -1066,6 +1071,10 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
     }
     g.sync();
     if (g.leader_warp()) {
+      if (pass == 0 && dup_known) {  // the count-1 entries: new entries less the marked slots
+        if (lane == 0) r.hist[0] += misc[10] - misc[5];
+        __syncwarp();
+      }
       uint32_t sum = 0;
 #pragma unroll
       for (int i = 0; i < 8; ++i) sum += r.hist[lane * 8 + i];
@@ -1129,24 +1138,21 @@ __device__ void select_from_table(const BlockGroup &g, const QArgs &a, const Reg
       nlist = misc[5];
     }
   }
-  g.sync();
-  if (g.rank() == 0) misc[5] = 0;
-  g.sync();
+  // the loop ended on a barrier: threshold, count and list are final
   const uint32_t thr = misc[4], nsel = misc[6];
   if (listed) {
     for (uint32_t base = 0; base < nlist; base += g.size()) {
       const uint32_t i = base + g.rank();
       const uint32_t key = i < nlist ? r.lst[i] : 0u;
-      append_warp(r.hist, 256u, &misc[5], i < nlist && key >= thr, key);
+      append_warp(r.hist, 256u, &misc[11], i < nlist && key >= thr, key);
     }
   } else {
     for_table_keys(r, S, [&](int, bool valid, uint32_t key) {
-      append_warp(r.hist, 256u, &misc[5], valid && key >= thr, key);
+      append_warp(r.hist, 256u, &misc[11], valid && key >= thr, key);
     });
   }
   g.sync();
-  block_rank_write(a, r.hist, nsel, q);
-  g.sync();
+  block_rank_write(a, r.hist, nsel, q);  // the caller's barrier follows
 }
 
 __device__ __forceinline__ unsigned long long claim_query(const QArgs &a) {
