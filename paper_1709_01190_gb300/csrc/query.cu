@@ -1278,14 +1278,18 @@ __global__ void __launch_bounds__(kBigThreads, 2) query_big_kernel(QArgs a, int 
         const uint32_t ntab = a.L > static_cast<uint32_t>(warp) ? (a.L - warp + kBigWarps - 1) / kBigWarps : 0;
         const uint32_t *wp = r.wpre + warp * (kMaxTabPerWarp + 1);
         const uint32_t nbatch = (r.misc[9] + 32 * kBatch - 1) / (32 * kBatch);
+        // the CAS count (one or two batches) probes a table twice the size when
+        // the region has room: at load <= 1/3 a warp's longest probe chain, which
+        // every lane of the warp waits for, is shorter
+        const uint32_t St = (nbatch <= 2 && 2 * S <= a.table_words) ? 2 * S : S;
         int32_t ids[kBatch];
         uint32_t cur = 0;
         load_stream_ids(a, wp, r.off + warp * kMaxTabPerWarp, wp[ntab], 0, cur, ids);
-        count_phase_block(g, a, r, q, nbatch, ids, cur, S);
+        count_phase_block(g, a, r, q, nbatch, ids, cur, St);
         if (a.k <= 256) {
-          select_from_table(g, a, r, q, S, nbatch <= 2);
+          select_from_table(g, a, r, q, St, nbatch <= 2);
         } else {
-          const uint32_t E = compact_keys(g, r.tab, r.aux, S, r.hist);
+          const uint32_t E = compact_keys(g, r.tab, r.aux, St, r.hist);
           select_phase(g, a, r, q, r.tab, E);
         }
       }
