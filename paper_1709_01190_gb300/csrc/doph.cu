@@ -249,21 +249,25 @@ __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const u
 // bins src_i = ((mix(d ^ (j * 2^32 + i)) >> 32) * B) >> 32, i = 1 .. 8B (mix =
 // SplitMix64's output function), and copies the first non-empty one; after 8B
 // misses it copies the first non-empty bin to its right, circularly.  Each
-// lane walks its own bins (lane, lane + 32, ...) so that the lanes' probe
-// counts even out over the row; only empty bins are written and only
-// non-empty ones read.
+// lane walks its own bins (lane, lane + 32, ...), four probes at a time, and
+// moves on to its next empty bin as soon as one is resolved: a warp then runs
+// for the longest lane's total, not for the longest single search of every
+// round of 32 bins (searches are geometric with mean B / non-empty bins, and
+// the longest of 32 is several times the mean).  Only empty bins are written
+// and only non-empty ones read.
 __device__ __forceinline__ bool bin_filled(const uint32_t *mask, uint32_t b) { return (mask[b >> 5] >> (b & 31)) & 1u; }
 
 template <bool PAD>
 __device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mask, uint32_t B, uint64_t d,
                                              uint32_t lane) {
   const uint32_t imax = 8u * B;  // a multiple of 4
-  for (uint32_t j = lane; j < B; j += 32) {
-    if (bin_filled(mask, j)) continue;
-    uint32_t src = 0xFFFFFFFFu;
-    const uint64_t key = d ^ (static_cast<uint64_t>(j) << 32);  // d ^ (j * 2^32 + i) = key ^ i for i < 2^32
-    // four probes at a time (independent mixes), the earliest hit wins
-    for (uint32_t i = 1; i <= imax && src == 0xFFFFFFFFu; i += 4) {
+  uint32_t j = lane;
+  while (j < B && bin_filled(mask, j)) j += 32;
+  uint32_t i = 1;
+  uint64_t key = d ^ (static_cast<uint64_t>(j) << 32);  // d ^ (j * 2^32 + i) = key ^ i for i < 2^32
+  while (__any_sync(kFull, j < B)) {
+    if (j < B) {
+      uint32_t src = 0xFFFFFFFFu;
       uint32_t pr[4];
       bool hit[4];
 #pragma unroll
@@ -273,20 +277,27 @@ __device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mas
         hit[q] = bin_filled(mask, pr[q]);
       }
 #pragma unroll
-      for (int q = 3; q >= 0; --q)
+      for (int q = 3; q >= 0; --q)  // the earliest hit of the four wins
         if (hit[q]) src = pr[q];
-    }
-    if (src == 0xFFFFFFFFu) {  // the next non-empty bin to the right, circularly (one exists)
-      src = j;
-      for (uint32_t t = 1; t <= B; ++t) {
-        const uint32_t b = j + t < B ? j + t : j + t - B;
-        if (bin_filled(mask, b)) {
-          src = b;
-          break;
+      i += 4;
+      if (src == 0xFFFFFFFFu && i > imax) {  // the next non-empty bin to the right, circularly (one exists)
+        src = j;
+        for (uint32_t t = 1; t <= B; ++t) {
+          const uint32_t b = j + t < B ? j + t : j + t - B;
+          if (bin_filled(mask, b)) {
+            src = b;
+            break;
+          }
         }
       }
+      if (src != 0xFFFFFFFFu) {
+        bins[bix<PAD>(j)] = bins[bix<PAD>(src)];
+        j += 32;
+        while (j < B && bin_filled(mask, j)) j += 32;
+        i = 1;
+        key = d ^ (static_cast<uint64_t>(j) << 32);
+      }
     }
-    bins[bix<PAD>(j)] = bins[bix<PAD>(src)];
   }
   __syncwarp();
 }
