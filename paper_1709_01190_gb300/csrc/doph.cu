@@ -249,24 +249,37 @@ __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const u
 // bins src_i = ((mix(d ^ (j * 2^32 + i)) >> 32) * B) >> 32, i = 1 .. 8B (mix =
 // SplitMix64's output function), and copies the first non-empty one; after 8B
 // misses it copies the first non-empty bin to its right, circularly.  Each
-// lane walks its own bins (lane, lane + 32, ...), four probes at a time, and
-// moves on to its next empty bin as soon as one is resolved: a warp then runs
-// for the longest lane's total, not for the longest single search of every
-// round of 32 bins (searches are geometric with mean B / non-empty bins, and
-// the longest of 32 is several times the mean).  Only empty bins are written
-// and only non-empty ones read.
+// lane searches one empty bin at a time, four probes a step; a lane whose
+// search ends takes the next unassigned bin of the row (a warp-uniform counter,
+// positions from a ballot), so the warp runs for about the row's total probes
+// over 32 lanes, not for the longest search of every round of 32 bins
+// (searches are geometric with mean B / non-empty bins, and the longest of 32
+// is several times the mean).  Only empty bins are written and only non-empty
+// ones read.
 __device__ __forceinline__ bool bin_filled(const uint32_t *mask, uint32_t b) { return (mask[b >> 5] >> (b & 31)) & 1u; }
 
 template <bool PAD>
 __device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mask, uint32_t B, uint64_t d,
                                              uint32_t lane) {
   const uint32_t imax = 8u * B;  // a multiple of 4
-  uint32_t j = lane;
-  while (j < B && bin_filled(mask, j)) j += 32;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t next = 0;  // warp-uniform: the first bin not yet assigned
+  uint32_t j = B;     // this lane's bin (B: none)
   uint32_t i = 1;
-  uint64_t key = d ^ (static_cast<uint64_t>(j) << 32);  // d ^ (j * 2^32 + i) = key ^ i for i < 2^32
-  while (__any_sync(kFull, j < B)) {
+  uint64_t key = 0;
+  bool want = true;  // this lane needs a bin
+  for (;;) {
+    // hand out bins until every lane that needs one holds an empty bin or the row is done
+    while (__any_sync(kFull, want)) {
+      const uint32_t req = __ballot_sync(kFull, want);
+      if (want) j = next + __popc(req & lt);
+      next += __popc(req);
+      want = want && j < B && bin_filled(mask, j);
+      if (j >= B) j = B;
+    }
+    if (!__any_sync(kFull, j < B)) break;
     if (j < B) {
+      if (i == 1) key = d ^ (static_cast<uint64_t>(j) << 32);  // d ^ (j * 2^32 + i) = key ^ i for i < 2^32
       uint32_t src = 0xFFFFFFFFu;
       uint32_t pr[4];
       bool hit[4];
@@ -292,10 +305,9 @@ __device__ __noinline__ void optimal_densify(uint32_t *bins, const uint32_t *mas
       }
       if (src != 0xFFFFFFFFu) {
         bins[bix<PAD>(j)] = bins[bix<PAD>(src)];
-        j += 32;
-        while (j < B && bin_filled(mask, j)) j += 32;
+        j = B;
         i = 1;
-        key = d ^ (static_cast<uint64_t>(j) << 32);
+        want = true;
       }
     }
   }
