@@ -58,6 +58,9 @@ struct DophParams {
   uint32_t *err;
   unsigned long long *row_counter;
   const int32_t *order;  // optional processing order of the rows (longest first)
+  const int32_t *long_rows;    // optional: long rows, hashed first
+  const uint32_t *long_count;  // their number (device)
+  int64_t long_min;            // non-zeros of a long row
 };
 
 // Shared-memory position of bin j.  Sparse rows keep one pad word after every
@@ -416,24 +419,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4) doph_kernel(DophParams
 
   // Rows are claimed G at a time from a global counter; each row's bounds are
   // read when the row starts (the 16-byte groups of the row are prefetched
-  // one group ahead).
+  // one group ahead).  With a list of long rows, positions [0, nl) are those
+  // rows and positions nl + r are the rows in index order, long ones skipped:
+  // a long row claimed late would outlast the rest of the launch.
+  const int64_t nl = a.long_rows ? static_cast<int64_t>(*a.long_count) : 0;
+  const int64_t total = nl + a.n_rows;
   int64_t cpos = 0, cend = 0;
   for (;;) {
     if (cpos >= cend) {
       unsigned long long s0 = 0;
       if (lane == 0) s0 = atomicAdd(a.row_counter, static_cast<unsigned long long>(G));
       s0 = __shfl_sync(kFull, s0, 0);
-      if (s0 >= static_cast<unsigned long long>(a.n_rows)) break;
+      if (s0 >= static_cast<unsigned long long>(total)) break;
       cpos = static_cast<int64_t>(s0);
-      cend = min(cpos + G, a.n_rows);
+      cend = min(cpos + G, total);
     }
     const int64_t pos = cpos++;
-    const int64_t r = a.order ? static_cast<int64_t>(a.order[pos]) : pos;
+    const bool listed = pos < nl;
+    const int64_t r = listed ? static_cast<int64_t>(a.long_rows[pos])
+                             : (a.order ? static_cast<int64_t>(a.order[pos - nl]) : pos - nl);
     int64_t start = a.row_ptr[r], end = a.row_ptr[r + 1];
     if (start < 0 || end < start || end > a.nnz) {
       if (lane == 0) raise_error(a.err, FLASH_DEVERR_ROW_PTR);
       start = end = 0;
     }
+    if (!listed && nl > 0 && end - start >= a.long_min) continue;  // hashed from the list
     const int64_t n = end - start;
     if (n == 0) {  // empty row: all-ones hashes; never inserted
       emit_empty<KEYS>(a, r, lane);
@@ -552,14 +562,26 @@ __global__ void row_class_scan_kernel(uint32_t *hist) {  // one thread: offsets,
   }
 }
 
+// rows of class >= cmin go to order[offs[class]++] (cmin = 0: every row)
 __global__ void __launch_bounds__(256) row_class_scatter_kernel(const int64_t *row_ptr, int64_t n, uint32_t *offs,
-                                                                int32_t *order) {
+                                                                int32_t *order, uint32_t cmin) {
   for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t m = row_ptr[r + 1] - row_ptr[r];
     const uint32_t c = m > 0 ? 64u - __clzll(static_cast<unsigned long long>(m)) : 0u;
-    order[atomicAdd(&offs[c], 1u)] = static_cast<int32_t>(r);
+    if (c >= cmin) order[atomicAdd(&offs[c], 1u)] = static_cast<int32_t>(r);
   }
+}
+
+// offsets of the classes >= cmin, largest class first; hist[40] = their rows
+__global__ void long_class_scan_kernel(uint32_t *hist, uint32_t cmin) {  // one thread
+  uint32_t run = 0;
+  for (int c = 39; c >= static_cast<int>(cmin); --c) {
+    const uint32_t v = hist[c];
+    hist[c] = run;
+    run += v;
+  }
+  hist[40] = run;
 }
 
 // 32 x 32 tiles (rows x tables): coalesced reads along the tables of a row,
@@ -614,7 +636,20 @@ int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t 
   if (blocks > 8L * num_sms()) blocks = 8L * num_sms();
   row_class_hist_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist40);
   row_class_scan_kernel<<<1, 1, 0, stream>>>(hist40);
-  row_class_scatter_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist40, order);
+  row_class_scatter_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist40, order, 0u);
+  count_launches(3);
+  return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
+}
+
+int build_long_rows(const int64_t *row_ptr, int64_t n, uint32_t cmin, int32_t *long_rows, uint32_t *hist41,
+                    cudaStream_t stream) {
+  if (cudaMemsetAsync(hist41, 0, 41 * sizeof(uint32_t), stream) != cudaSuccess) return FLASH_ECUDA;
+  if (n <= 0) return 0;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 8L * num_sms()) blocks = 8L * num_sms();
+  row_class_hist_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist41);
+  long_class_scan_kernel<<<1, 1, 0, stream>>>(hist41, cmin);
+  row_class_scatter_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(row_ptr, n, hist41, long_rows, cmin);
   count_launches(3);
   return cudaGetLastError() == cudaSuccess ? 0 : FLASH_ECUDA;
 }
@@ -645,6 +680,9 @@ int launch_doph(const DophLaunch &L, cudaStream_t stream) {
   a.err = L.err;
   a.row_counter = L.row_counter;
   a.order = L.order;
+  a.long_rows = L.long_rows;
+  a.long_count = L.long_count;
+  a.long_min = L.long_min;
   const double avg = L.n_rows > 0 ? static_cast<double>(L.nnz) / static_cast<double>(L.n_rows) : 1.0;
   // short rows are claimed several at a time; at most 16, so that the rows in
   // flight stay few enough for their table-major keys to meet in L2 (64 per

@@ -201,19 +201,43 @@ DophLaunch doph_args(const flash_params *p, const Seeds &s, const flash_csr *x, 
 }
 
 // Optional longest-rows-first order of the rows for the DOPH kernel.
+// The DOPH processing order: index order (the default), longest rows first
+// (tuning doph_order = 1), or, with allow_long and rows of at least 512
+// non-zeros on average, index order after a list of the rows with at least 4x
+// the average (rounded up to a power of two), longest class first: one warp
+// hashes a row, and a very long row claimed late would outlast the launch
+// (webspam-like rows: warps finished at 855 us, the last at 960 us).  The list
+// is reserved whenever it is allowed, so that scratch sizes depend on the row
+// count alone.
 struct RowOrder {
   int32_t *order = nullptr;
   uint32_t *hist = nullptr;
-  void plan(Arena &ar, const flash_tuning &tu, int64_t n) {
+  int32_t *long_rows = nullptr;
+  void plan(Arena &ar, const flash_tuning &tu, int64_t n, bool allow_long = false) {
     if (tu.doph_order == 1 && n > 0) {
       ar.add(&order, n);
       ar.add(&hist, 40);
+    } else if (allow_long && n > 0) {
+      ar.add(&long_rows, n);
+      ar.add(&hist, 41);
     }
   }
   int apply(DophLaunch &d, const flash_csr *x, cudaStream_t st) {
-    if (!order) return 0;
-    d.order = order;
-    return build_row_order(x->row_ptr, x->n_rows, order, hist, st);
+    if (order) {
+      d.order = order;
+      return build_row_order(x->row_ptr, x->n_rows, order, hist, st);
+    }
+    if (long_rows && x->n_rows > 0 && x->nnz >= 512 * x->n_rows) {
+      int64_t long_min = 1;
+      while (long_min < 4 * (x->nnz / x->n_rows)) long_min <<= 1;
+      uint32_t cmin = 1;  // the log2 class of long_min: floor(log2 m) + 1
+      while ((int64_t{1} << (cmin - 1)) < long_min) ++cmin;
+      d.long_rows = long_rows;
+      d.long_count = hist + 40;
+      d.long_min = long_min;
+      return build_long_rows(x->row_ptr, x->n_rows, cmin, long_rows, hist, st);
+    }
+    return 0;
   }
 };
 
@@ -243,7 +267,7 @@ void plan_build(Arena &ar, BuildScratch &b, const flash_params *p, int64_t n, in
   b.transpose = nnz < static_cast<int64_t>(p->L) * n;
   if (b.transpose) rowmajor_keys = true;
   b.tu = current_tuning();
-  b.ro.plan(ar, b.tu, n);
+  b.ro.plan(ar, b.tu, n, true);
   b.plan = make_sort_plan(p->range_bits, n, p->L);
   b.heavy_cap = reservoir_heavy_capacity(n, p->L, p->R, p->range_bits);
   ar.add(&b.keys, ln);
@@ -281,7 +305,7 @@ struct SharedScratch {
 void plan_build_shared(Arena &ar, SharedScratch &b, const flash_params *p, int64_t n) {
   const int64_t ln = static_cast<int64_t>(p->L) * n;
   b.tu = current_tuning();
-  b.ro.plan(ar, b.tu, n);
+  b.ro.plan(ar, b.tu, n, true);
   b.pool_bits = pool_bits_of(p->share_pool);
   b.plan = make_sort_plan(b.pool_bits, ln, 1);
   b.heavy_cap = reservoir_heavy_capacity(ln, 1, p->R, b.pool_bits);
@@ -452,7 +476,7 @@ int flash_hash(const flash_params *p, const flash_csr *x, uint32_t *hashes, void
   unsigned long long *counter = nullptr;
   RowOrder ro;
   ar.add(&counter, 1);
-  ro.plan(ar, tu, x->n_rows);
+  ro.plan(ar, tu, x->n_rows, true);
   if (int rc = ar.alloc(st)) return rc;
   flash_params q = *p;
   q.range_bits = 1;
@@ -479,7 +503,7 @@ int flash_keys(const flash_params *p, const flash_csr *x, uint32_t *keys, void *
   RowOrder ro;
   ar.add(&counter, 1);
   if (transpose) ar.add(&rm, static_cast<int64_t>(p->L) * x->n_rows);
-  ro.plan(ar, tu, x->n_rows);
+  ro.plan(ar, tu, x->n_rows, true);
   if (int rc = ar.alloc(st)) return rc;
   DophLaunch dl = doph_args(p, derive_seeds(p->seed), x, true, transpose ? nullptr : keys, x->n_rows, counter, tu);
   dl.out_rowmajor = rm;

@@ -45,6 +45,11 @@ struct DophLaunch {
   uint32_t rows_per_grab;           // 0 = automatic
   int64_t max_blocks;               // 0 = automatic
   const int32_t *order;             // optional row processing order (null = 0..n-1)
+  // optional: rows with at least long_min non-zeros, listed in long_rows[0 .. *long_count)
+  // (longest class first), are hashed first and then skipped in index order
+  const int32_t *long_rows;
+  const uint32_t *long_count;
+  int64_t long_min;
 };
 int launch_doph(const DophLaunch &l, cudaStream_t stream);
 // keys [n][L] (row-major) -> keys [L][ld] (table-major), tiled through shared memory
@@ -52,6 +57,10 @@ int launch_transpose_keys(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *t
 // order[0..n) = row ids, longest rows first (rows binned by log2 of their length);
 // hist40: 40 words of scratch
 int build_row_order(const int64_t *row_ptr, int64_t n, int32_t *order, uint32_t *hist40, cudaStream_t stream);
+// long_rows[0 .. hist41[40]) = the rows with at least 2^(cmin - 1) non-zeros (log2
+// class >= cmin), longest class first; hist41: 41 words of scratch
+int build_long_rows(const int64_t *row_ptr, int64_t n, uint32_t cmin, int32_t *long_rows, uint32_t *hist41,
+                    cudaStream_t stream);
 
 // ---- K2: per-table stable sort of bucket addresses + bucket starts
 // (partition by the high bits, then one warp per segment on the low bits)
