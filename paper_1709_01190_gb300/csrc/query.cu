@@ -1372,7 +1372,13 @@ int launch_query(const QueryLaunch &l, cudaStream_t stream) {
   const uint32_t full_table = next_pow2(2 * l.L * l.R) < 64 ? 64 : next_pow2(2 * l.L * l.R);
   uint32_t tw = l.warp_table ? l.warp_table : 512u;
   if (tw > full_table) tw = full_table;
-  const bool warp_ok = l.k <= 256 && !(l.exclude_self && 2 * l.L >= tw);
+  // It is skipped too when the index's buckets hold so many points that a
+  // typical query would not fit either: expected candidates L * min(points per
+  // bucket, R) above twice what the warp table takes (tw / 2).
+  const double per_bucket = (l.shared ? static_cast<double>(l.L) * l.n : static_cast<double>(l.n)) / a.T;
+  const double expected_m = static_cast<double>(l.L) * (per_bucket < l.R ? per_bucket : static_cast<double>(l.R));
+  const bool mostly_big = expected_m > static_cast<double>(tw);
+  const bool warp_ok = l.k <= 256 && !(l.exclude_self && 2 * l.L >= tw) && !mostly_big;
   int all = 1;
   if (warp_ok) {
     a.table_words = tw;
