@@ -217,19 +217,36 @@ __device__ __forceinline__ void dense_mask(const DophParams &a, const uint32_t *
   __syncwarp();
 }
 
+// The L keys of row r from its B final bins (MapKHashesToAddress), with the
+// number of hashes per table fixed at compile time (KC > 0: the Horner fold
+// unrolls) or read from the arguments (KC = 0).
+template <int KC, bool PAD>
+__device__ __forceinline__ void emit_keys(const DophParams &a, int64_t r, const uint32_t *bins, uint32_t lane) {
+  const uint32_t K = KC > 0 ? static_cast<uint32_t>(KC) : a.K;
+  const int sh = 64 - static_cast<int>(a.rb);
+  const uint64_t a2 = a.s.a2, b2 = a.s.b2;
+  for (uint32_t t = lane; t < a.L; t += 32) {
+    uint64_t x = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < K; ++i) x = x * a2 + bins[bix<PAD>(t + i * a.L)];
+    uint32_t key = static_cast<uint32_t>((a2 * x + b2) >> sh);
+    if (a.pool) key = pool_index(a.s.e, t, key, a.pool);  // the shared reservoir the bucket points to
+    if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
+    if (a.out_rm) a.out_rm[r * a.L + t] = key;
+  }
+}
+
 // The emit of row r from its B final bins: the L keys or the B hashes.
 template <bool KEYS, bool PAD>
 __device__ __forceinline__ void emit_row(const DophParams &a, int64_t r, const uint32_t *bins, uint32_t lane) {
   const uint32_t B = a.B;
   if (KEYS) {
-    const int sh = 64 - static_cast<int>(a.rb);
-    for (uint32_t t = lane; t < a.L; t += 32) {
-      uint64_t x = 0;
-      for (uint32_t i = 0; i < a.K; ++i) x = x * a.s.a2 + bins[bix<PAD>(t + i * a.L)];
-      uint32_t key = static_cast<uint32_t>((a.s.a2 * x + a.s.b2) >> sh);
-      if (a.pool) key = pool_index(a.s.e, t, key, a.pool);  // the shared reservoir the bucket points to
-      if (a.out) a.out[static_cast<int64_t>(t) * a.ld + r] = key;
-      if (a.out_rm) a.out_rm[r * a.L + t] = key;
+    switch (a.K) {
+      case 4: emit_keys<4, PAD>(a, r, bins, lane); break;
+      case 3: emit_keys<3, PAD>(a, r, bins, lane); break;
+      case 2: emit_keys<2, PAD>(a, r, bins, lane); break;
+      case 1: emit_keys<1, PAD>(a, r, bins, lane); break;
+      default: emit_keys<0, PAD>(a, r, bins, lane); break;
     }
   } else if (a.vec_out && !PAD) {
     uint4 *o = reinterpret_cast<uint4 *>(a.out + r * B);
