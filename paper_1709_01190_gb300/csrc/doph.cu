@@ -369,17 +369,19 @@ __device__ __forceinline__ void finish_row(const DophParams &a, int64_t r, uint3
       const int w2 = next_word_circular(sw, a.G, w + 1 < W ? w + 1 : 0);
       const uint32_t m2 = mask[w2];
       const uint32_t s2 = 32u * static_cast<uint32_t>(w2) + (__ffs(m2) - 1);
-      uint32_t cur = s2 + (static_cast<uint32_t>(w2) <= w ? B : 0u);  // wrapped: distance counts B
-      uint32_t curv = bins[bix<true>(s2)];
+      const uint32_t cur = s2 + (static_cast<uint32_t>(w2) <= w ? B : 0u);  // wrapped: distance counts B
       const uint32_t j0 = 32u * w;
+      // v = the value of bin j + 1 on the way down: an empty bin j takes v + C
+      // (= v[src] + (src - j) * C), a filled one its own value
+      uint32_t v = bins[bix<true>(s2)] + (cur - (j0 + 32u)) * kRotStep;
 #pragma unroll
       for (int b = 31; b >= 0; --b) {
         const uint32_t j = j0 + b;
         if ((m >> b) & 1u) {
-          cur = j;
-          curv = bins[bix<true>(j)];
+          v = bins[bix<true>(j)];
         } else {
-          bins[bix<true>(j)] = curv + (cur - j) * kRotStep;  // bins past B (last word) are never read
+          v += kRotStep;
+          bins[bix<true>(j)] = v;  // bins past B (last word) are never read
         }
       }
     }
