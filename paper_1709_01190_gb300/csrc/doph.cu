@@ -605,32 +605,47 @@ __global__ void long_class_scan_kernel(uint32_t *hist, uint32_t cmin) {  // one 
 
 // 32 x 32 tiles (rows x tables): coalesced reads along the tables of a row,
 // coalesced writes along the rows of a table.  A grid of a few blocks per SM
-// walks the tiles (one tile per block would make millions of tiny blocks at
-// L = 256); each thread has its four loads in flight before it stores.
+// walks the tiles two at a time (one tile per block would make millions of
+// tiny blocks at L = 256); each thread has its eight loads in flight before it
+// stores.
 __global__ void __launch_bounds__(256) transpose_keys_kernel(const uint32_t *rm, int64_t n, uint32_t L, uint32_t *tm,
                                                               int64_t ld) {
-  __shared__ uint32_t tile[32][33];
+  __shared__ uint32_t tile[2][32][33];
   const uint32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t row_tiles = (n + 31) / 32;
   const int64_t tiles = row_tiles * ((L + 31) / 32);
-  for (int64_t ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
-    const int64_t r0 = (ti % row_tiles) * 32;
-    const uint32_t t0 = static_cast<uint32_t>(ti / row_tiles) * 32;
-    uint32_t v[4];
+  for (int64_t ti = blockIdx.x; ti < tiles; ti += 2LL * gridDim.x) {
+    uint32_t v[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t r = r0 + ty + 8 * i;
-      const uint32_t t = t0 + tx;
-      v[i] = (r < n && t < L) ? __ldcs(rm + r * L + t) : 0u;
+    for (int u = 0; u < 2; ++u) {
+      const int64_t tu = ti + u * static_cast<int64_t>(gridDim.x);
+      const int64_t r0 = (tu % row_tiles) * 32;
+      const uint32_t t0 = static_cast<uint32_t>(tu / row_tiles) * 32;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + ty + 8 * i;
+        const uint32_t t = t0 + tx;
+        v[u][i] = (tu < tiles && r < n && t < L) ? __ldcs(rm + r * L + t) : 0u;
+      }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) tile[ty + 8 * i][tx] = v[i];
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) tile[u][ty + 8 * i][tx] = v[u][i];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t t = t0 + ty + 8 * i;
-      const int64_t r = r0 + tx;
-      if (r < n && t < L) tm[static_cast<int64_t>(t) * ld + r] = tile[tx][ty + 8 * i];
+    for (int u = 0; u < 2; ++u) {
+      const int64_t tu = ti + u * static_cast<int64_t>(gridDim.x);
+      if (tu < tiles) {
+        const int64_t r0 = (tu % row_tiles) * 32;
+        const uint32_t t0 = static_cast<uint32_t>(tu / row_tiles) * 32;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t t = t0 + ty + 8 * i;
+          const int64_t r = r0 + tx;
+          if (r < n && t < L) tm[static_cast<int64_t>(t) * ld + r] = tile[u][tx][ty + 8 * i];
+        }
+      }
     }
     __syncthreads();
   }
