@@ -100,7 +100,31 @@ def test_doph_long_rows_every_length_class(order):
     assert fl.flash_device_error() == 0
 
 
+@pytest.mark.parametrize("lens", [
+    [600] * 300 + [30_000] * 6,       # the long rows last in index order
+    [10] * 800 + [5_000] * 200,       # a fifth of the rows long
+    [200_000] + [10] * 7,             # one long row first, the rest tiny
+])
+def test_doph_long_rows_hashed_first(lens):
+    """With rows of 512 or more non-zeros on average, the rows of at least 4x the average length
+    (rounded up to a power of two) are hashed first and then skipped in index order: keys and
+    hashes equal the oracle's wherever the long rows sit."""
+    rng = np.random.default_rng(len(lens))
+    dim = 1 << 22
+    rows = [list(rng.integers(0, dim, m)) for m in lens]
+    c = csr_of(rows, dim)
+    assert c.row_ptr[-1] >= 512 * len(lens)
+    p = fl.FlashParams(4, 64, 4, 14, 0x51ED)
+    dev = fl.DeviceCSR.from_host(c)
+    got_k = u32(fl.row_keys(p, dev))
+    got_h = u32(fl.hash_rows(p, dev))
+    assert np.array_equal(got_k, oracle.keys(c.row_ptr, c.col, p.K, p.L, p.range_bits, p.seed))
+    assert np.array_equal(got_h, oracle.doph(c.row_ptr, c.col, p.K, p.L, p.seed))
+    assert fl.flash_device_error() == 0
+
+
 # ---------------------------------------------- optimal densification ([36])
+
 
 @pytest.mark.parametrize("K,L", [(1, 1), (3, 5), (4, 16), (2, 33), (4, 256), (8, 512)])
 def test_doph_optimal_densification_adversarial(K, L):
