@@ -954,12 +954,14 @@ __device__ __forceinline__ void for_table_keys(const Region &r, uint32_t S, F &&
 // Block-path selection, k <= 256: a radix select over the sort keys
 // (count - 1) << 24 | (2^24 - 1 - id), 8-bit digits from the top, that stops
 // at the first digit where at most 256 keys reach the threshold; those keys
-// are collected and sorted by one warp, which writes the k best.  Exactly one
-// key remains in the threshold digit after the last pass (keys are
+// are collected and the block writes the k best, each at its rank.  Exactly
+// one key remains in the threshold digit after the last pass (keys are
 // distinct), so it always stops by then.
-// The first pass (the count digit) reads the table: count-1 entries, nearly
-// all of them, are only tallied per thread, and the keys of entries with
-// count >= 2 are gathered into a list on the way (up to kListCap).  Later
+// The first pass (the count digit) builds the count histogram and gathers the
+// keys of entries with count >= 2 into a list (up to kListCap): with dup_known
+// (the CAS count marked the slots of ids that arrived again) it reads only the
+// marked slots; otherwise it reads the table, tallying the count-1 entries,
+// nearly all of them, per thread.  Later
 // passes read that list when the threshold count is >= 2 and the list is
 // complete; otherwise they read the table, and the keys reaching the
 // threshold are gathered into the list once there are at most kListCap.

@@ -298,7 +298,7 @@ QUERY_CASES = [
     ("tiny_plain", 3_000, dict(range_bits=5, R=8), 300, 0),      # k > 256: block path only
     # block path, second tier: most reservoirs full (M near L*R = 16384 > the 64 KB table's 10922)
     ("url_like_batched", 20_000, dict(range_bits=6, K=1), 64, 0),
-    # both block tiers mixed (M spread around 10922), k = 200 sorted by one warp
+    # both block tiers mixed (M spread around 10922), k = 200 written at their ranks by the block
     ("url_like_batched", 20_000, dict(range_bits=8, K=1), 200, 64),
     # k > 256 with second-tier queries: every query on the block path, block bitonic sort
     ("url_like_batched", 20_000, dict(range_bits=7, K=1), 300, 0),
